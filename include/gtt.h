@@ -1,0 +1,170 @@
+/*
+ * gtt.h -- C ABI of the GB300 Generalized Tensor Transform library (libgtt.so).
+ *
+ * The transform (Def. 2.3 of arXiv 2507.02420, "Generalized tensor
+ * transforms and their applications in classical and quantum computing"):
+ *
+ *     y = G_N x,   G_N = W (x) W (x) ... (x) W  (n factors),   N = b^n,
+ *
+ * for a b x b base matrix W.  Element form (Sec. 2.6):
+ *
+ *     y[p] = sum_q prod_{j=0}^{n-1} W[p_j][q_j] x[q],
+ *
+ * where p = sum_j p_j b^j and q = sum_j q_j b^j are base-b digit expansions
+ * (digit 0 least significant) and W[i][j] is row i, column j, 0-based
+ * (Sec. 2.1).  This is the "natural ordering" of the paper: no digit
+ * reversal and no sequency reordering.  The fast algorithm of Sec. 3
+ * (Algorithm 1) applies W to one digit at a time; its cost is O(N b log_b N).
+ *
+ * Conventions shared by every call below
+ * --------------------------------------
+ * - Vectors are contiguous and batch-major: `batch` vectors of N elements,
+ *   vector v occupying elements [v*N, (v+1)*N).
+ * - Element types (gtt_dtype_t): F64 = double, F32 = float, C64 = interleaved
+ *   (float re, float im), C128 = interleaved (double re, double im),
+ *   I32 = int32 whose arithmetic wraps modulo 2^32 (computed in uint32).
+ * - Device pointers (x, y, dx, dy) must be 16-byte aligned device memory of
+ *   the plan's device; a misaligned or NULL pointer returns
+ *   GTT_ERR_INVALID_ARG.  The caller owns them.  In-place use (y == x) is
+ *   allowed; partially overlapping buffers are not.
+ * - Every device call is asynchronous on `stream` (a cudaStream_t passed as
+ *   void*; NULL is the legacy default stream).  Errors are returned as status
+ *   codes and never abort the process; gtt_last_error() gives a message for
+ *   the calling thread.  CUDA errors map to GTT_ERR_CUDA.
+ * - A plan may be used from one host thread at a time.
+ */
+#ifndef GTT_H_
+#define GTT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gtt_plan_s *gtt_plan_t;
+typedef struct gtt_group_s *gtt_group_t;
+typedef void *gtt_stream_t; /* cudaStream_t */
+
+typedef enum {
+    GTT_F64 = 0,
+    GTT_F32 = 1,
+    GTT_C64 = 2,
+    GTT_C128 = 3,
+    GTT_I32 = 4
+} gtt_dtype_t;
+
+typedef enum {
+    GTT_OK = 0,
+    GTT_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or enum value      */
+    GTT_ERR_UNSUPPORTED = 2, /* valid request this build does not implement      */
+    GTT_ERR_ALLOC = 3,       /* device or host allocation failed                 */
+    GTT_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed      */
+    GTT_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired               */
+    GTT_ERR_INTERNAL = 6
+} gtt_status_t;
+
+/* Arithmetic used for the b >= 16 contractions (gtt_plan_set_precision). */
+typedef enum {
+    GTT_PREC_AUTO = 0,   /* library choice (FP32 CUDA-core)                         */
+    GTT_PREC_FP32 = 1,   /* FP32 FMA on CUDA cores                                  */
+    GTT_PREC_BF16X3 = 2  /* tcgen05 BF16 products of 3-piece splits, FP32 accumulate */
+} gtt_precision_t;
+
+/*
+ * gtt_plan_create -- validate a transform and prepare it on the current CUDA
+ * device.  Definition: Def. 2.3 (G_N = W^{(x)n}).
+ *   out    receives the plan (owned by the caller; free with gtt_plan_destroy).
+ *   b      base, 2 <= b <= 16.
+ *   n      number of digits, n >= 1; N = b^n.
+ *   W      HOST pointer to b*b elements of `dtype`'s element type, row-major
+ *          (W[i*b + j] is row i, column j).  Copied; the caller keeps ownership.
+ *          For GTT_I32 the entries are int32.
+ *   dtype  element type of W, x and y.
+ *   batch  number of vectors per call, >= 1.
+ * The plan owns device copies of W, of W^H (W^T for real types) and of any
+ * workspace, and a fusion schedule (mode groups and tile shapes) chosen from
+ * the autotune cache when one is loaded, else by a fixed rule.
+ * Errors: GTT_ERR_INVALID_ARG (b, n, batch or dtype out of range, NULL out/W,
+ * batch*N above 2^40 elements), GTT_ERR_ALLOC, GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_dtype_t dtype,
+                             long long batch);
+
+/* Select the arithmetic of the b = 16 contraction (gtt_precision_t).  Other b
+ * accept GTT_PREC_AUTO and GTT_PREC_FP32 only.  GTT_PREC_BF16X3 requires b = 16
+ * and dtype F32; otherwise GTT_ERR_UNSUPPORTED. */
+gtt_status_t gtt_plan_set_precision(gtt_plan_t plan, int precision);
+
+/*
+ * gtt_plan_set_schedule -- replace the plan's fusion schedule by the fixed
+ * rule with the given limits: passes whose tiles hold at most max_tile_bytes
+ * (one shared-memory tile per CTA, <= 220 KiB) and, for passes above the
+ * lowest digits, contiguous runs of at least min_run_bytes where the lower
+ * digits allow it.  Used by the autotuner and by tests that sweep schedules.
+ * Errors: GTT_ERR_INVALID_ARG (limits out of range), GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_plan_set_schedule(gtt_plan_t plan, long long max_tile_bytes,
+                                   long long min_run_bytes);
+
+/*
+ * gtt_forward -- y = G_N x for each of the plan's `batch` vectors, natural
+ * ordering (Sec. 2.6 element form; Sec. 3 fast algorithm).
+ *   x  device, batch*N elements (read).   y  device, batch*N elements (written).
+ */
+gtt_status_t gtt_forward(gtt_plan_t plan, const void *x, void *y, gtt_stream_t stream);
+
+/*
+ * gtt_inverse -- x = (W^H)^{(x)n} y = G_N^dagger y (Sec. 4: the inverse GTT used
+ * for reconstruction).  This is the adjoint transform; it equals G_N^{-1}
+ * only when W is unitary.  For the +-1 integer Hadamard W it returns 2^n x.
+ */
+gtt_status_t gtt_inverse(gtt_plan_t plan, const void *y, void *x, gtt_stream_t stream);
+
+/*
+ * gtt_backward -- reverse-mode derivative of y = G_N x for a real loss L
+ * (not in the paper; PyTorch's conjugate convention for complex types):
+ *     dx = (W^H)^{(x)n} dy,
+ *     dW = sum_k sum_{mode-k fibres} g_{k+1} a_k^H,
+ * with a_0 = x, a_{k+1} the result of applying W to digit k of a_k, and
+ * g_{k+1} = dL/da_{k+1}.
+ *   x_saved  device, batch*N elements: the forward input.
+ *   dy       device, batch*N elements: dL/dy.
+ *   dx       device, batch*N elements or NULL (not computed).
+ *   dW       device, b*b elements of the element type, row-major, or NULL;
+ *            overwritten with the sum over the whole batch.  The sum is taken
+ *            in a fixed order, so repeated calls give identical bits.
+ * dx may alias dy.  Floating-point dtypes only (GTT_ERR_UNSUPPORTED for I32).
+ */
+gtt_status_t gtt_backward(gtt_plan_t plan, const void *x_saved, const void *dy, void *dx, void *dW,
+                          gtt_stream_t stream);
+
+/*
+ * gtt_forward_host / gtt_inverse_host -- the same transforms on HOST buffers:
+ * copy x (batch*N elements) to plan-owned device memory, transform, copy the
+ * result back into y, and wait for `stream`.  Host buffers may be pageable;
+ * page-locked buffers copy faster.  The device staging buffer is allocated on
+ * the first call and kept by the plan.
+ */
+gtt_status_t gtt_forward_host(gtt_plan_t plan, const void *x_host, void *y_host,
+                              gtt_stream_t stream);
+gtt_status_t gtt_inverse_host(gtt_plan_t plan, const void *y_host, void *x_host,
+                              gtt_stream_t stream);
+
+/*
+ * gtt_plan_describe -- write a one-line JSON description of the plan's
+ * schedule (passes, digits per pass, run length, tile bytes, kernels
+ * launched per transform) into buf (NUL-terminated, truncated to len).
+ */
+gtt_status_t gtt_plan_describe(gtt_plan_t plan, char *buf, size_t len);
+
+/* Release the plan and everything it owns.  NULL is accepted. */
+gtt_status_t gtt_plan_destroy(gtt_plan_t plan);
+
+/* Message describing the last error raised on the calling thread ("" if none). */
+const char *gtt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GTT_H_ */

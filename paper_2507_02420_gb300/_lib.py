@@ -1,0 +1,69 @@
+"""ctypes loader for libgtt.so: argument marshalling only.
+
+There is no fallback: if the library is missing or does not load, every call
+raises.  Build it with ``python -m paper_2507_02420_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgtt.so")
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+_S = ctypes.c_size_t
+
+# name -> (restype, argtypes), mirroring include/gtt.h
+SIGNATURES = {
+    "gtt_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I, _LL]),
+    "gtt_plan_set_precision": (_I, [_P, _I]),
+    "gtt_plan_set_schedule": (_I, [_P, _LL, _LL]),
+    "gtt_forward": (_I, [_P, _P, _P, _P]),
+    "gtt_inverse": (_I, [_P, _P, _P, _P]),
+    "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),
+    "gtt_forward_host": (_I, [_P, _P, _P, _P]),
+    "gtt_inverse_host": (_I, [_P, _P, _P, _P]),
+    "gtt_plan_describe": (_I, [_P, ctypes.c_char_p, _S]),
+    "gtt_plan_destroy": (_I, [_P]),
+    "gtt_last_error": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                              "(python -m paper_2507_02420_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+STATUS = {0: "GTT_OK", 1: "GTT_ERR_INVALID_ARG", 2: "GTT_ERR_UNSUPPORTED", 3: "GTT_ERR_ALLOC",
+          4: "GTT_ERR_CUDA", 5: "GTT_ERR_TIMEOUT", 6: "GTT_ERR_INTERNAL"}
+
+
+class GTTError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().gtt_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != 0:
+        raise GTTError(status, where)

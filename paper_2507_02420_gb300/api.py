@@ -1,0 +1,157 @@
+"""Python binding of libgtt: the same calls as include/gtt.h, with torch
+tensors for device memory and torch's current stream.  Only argument
+marshalling happens here; every step of the transform runs in the library's
+CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+
+import numpy as np
+import torch
+
+from ._lib import check, load
+
+F64, F32, C64, C128, I32 = 0, 1, 2, 3, 4
+PREC_AUTO, PREC_FP32, PREC_BF16X3 = 0, 1, 2
+
+_TORCH_DT = {F64: torch.float64, F32: torch.float32, C64: torch.complex64,
+             C128: torch.complex128, I32: torch.int32}
+_NP_DT = {F64: np.float64, F32: np.float32, C64: np.complex64, C128: np.complex128,
+          I32: np.int32}
+_FROM_TORCH = {v: k for k, v in _TORCH_DT.items()}
+_NAMES = {"f64": F64, "f32": F32, "c64": C64, "c128": C128, "i32": I32}
+
+
+def dtype_code(dt) -> int:
+    if isinstance(dt, int):
+        return dt
+    if isinstance(dt, str):
+        return _NAMES[dt]
+    if isinstance(dt, torch.dtype):
+        return _FROM_TORCH[dt]
+    return _FROM_TORCH[torch.from_numpy(np.zeros(1, dtype=dt)).dtype]
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _w_host_bytes(W, code: int) -> np.ndarray:
+    if isinstance(W, torch.Tensor):
+        W = W.detach().cpu().numpy()
+    W = np.asarray(W)
+    if code == I32:
+        W = (W.astype(np.int64) & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
+    return np.ascontiguousarray(W.astype(_NP_DT[code]) if code != I32 else W)
+
+
+class Plan:
+    """gtt_plan_t: a b x b base matrix W, n digits, an element type and a batch."""
+
+    def __init__(self, W, n: int, dtype=None, batch: int = 1):
+        lib = load()
+        Wn = W.detach().cpu().numpy() if isinstance(W, torch.Tensor) else np.asarray(W)
+        if Wn.ndim != 2 or Wn.shape[0] != Wn.shape[1]:
+            raise ValueError("W must be a square b x b matrix")
+        code = dtype_code(dtype if dtype is not None else Wn.dtype)
+        self.b, self.n, self.dtype, self.batch = int(Wn.shape[0]), int(n), code, int(batch)
+        self.N = self.b ** self.n
+        self._W = _w_host_bytes(Wn, code)
+        h = ctypes.c_void_p()
+        check(lib.gtt_plan_create(ctypes.byref(h), self.b, self.n,
+                                  self._W.ctypes.data_as(ctypes.c_void_p), code, self.batch),
+              "gtt_plan_create")
+        self._h = h
+        self._lib = lib
+
+    @property
+    def torch_dtype(self) -> torch.dtype:
+        return _TORCH_DT[self.dtype]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gtt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, prec: int):
+        check(self._lib.gtt_plan_set_precision(self._h, int(prec)), "gtt_plan_set_precision")
+
+    def set_schedule(self, max_tile_bytes: int, min_run_bytes: int = 128):
+        check(self._lib.gtt_plan_set_schedule(self._h, int(max_tile_bytes), int(min_run_bytes)),
+              "gtt_plan_set_schedule")
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(16384)
+        check(self._lib.gtt_plan_describe(self._h, buf, len(buf)), "gtt_plan_describe")
+        return json.loads(buf.value.decode())
+
+    # ---------------------------------------------------------- device calls
+    def _check_dev(self, t: torch.Tensor, name: str):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.torch_dtype:
+            raise TypeError(f"{name} has dtype {t.dtype}, plan expects {self.torch_dtype}")
+        if not t.is_contiguous() or t.numel() != self.batch * self.N:
+            raise ValueError(f"{name} must be contiguous with batch*N = {self.batch * self.N} elements")
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        self._check_dev(x, "x")
+        y = torch.empty_like(x) if out is None else out
+        self._check_dev(y, "out")
+        check(self._lib.gtt_forward(self._h, x.data_ptr(), y.data_ptr(), _stream_ptr(stream)),
+              "gtt_forward")
+        return y
+
+    def inverse(self, y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        self._check_dev(y, "y")
+        x = torch.empty_like(y) if out is None else out
+        self._check_dev(x, "out")
+        check(self._lib.gtt_inverse(self._h, y.data_ptr(), x.data_ptr(), _stream_ptr(stream)),
+              "gtt_inverse")
+        return x
+
+    def backward(self, x: torch.Tensor, dy: torch.Tensor, need_dx: bool = True,
+                 need_dW: bool = True, stream=None):
+        self._check_dev(x, "x")
+        self._check_dev(dy, "dy")
+        dx = torch.empty_like(dy) if need_dx else None
+        dW = torch.empty((self.b, self.b), dtype=self.torch_dtype, device=dy.device) if need_dW else None
+        check(self._lib.gtt_backward(self._h, x.data_ptr(), dy.data_ptr(),
+                                     dx.data_ptr() if dx is not None else None,
+                                     dW.data_ptr() if dW is not None else None,
+                                     _stream_ptr(stream)), "gtt_backward")
+        return dx, dW
+
+    # ------------------------------------------------------------ host calls
+    def _host_arrays(self, x):
+        xa = x.numpy() if isinstance(x, torch.Tensor) else np.asarray(x)
+        if xa.dtype != _NP_DT[self.dtype] or not xa.flags.c_contiguous or xa.size != self.batch * self.N:
+            raise ValueError("host buffer must be a contiguous array of the plan's dtype and size")
+        return xa
+
+    def forward_host(self, x, out=None, stream=None):
+        """y = G_N x on HOST buffers (numpy arrays or CPU tensors); blocks."""
+        xa = self._host_arrays(x)
+        y = np.empty_like(xa) if out is None else out
+        ya = self._host_arrays(y)
+        check(self._lib.gtt_forward_host(self._h, xa.ctypes.data, ya.ctypes.data, _stream_ptr(stream)),
+              "gtt_forward_host")
+        return y
+
+    def inverse_host(self, y, out=None, stream=None):
+        ya = self._host_arrays(y)
+        x = np.empty_like(ya) if out is None else out
+        xa = self._host_arrays(x)
+        check(self._lib.gtt_inverse_host(self._h, ya.ctypes.data, xa.ctypes.data, _stream_ptr(stream)),
+              "gtt_inverse_host")
+        return x

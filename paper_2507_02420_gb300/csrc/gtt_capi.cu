@@ -1,0 +1,344 @@
+// C ABI of libgtt (declared in include/gtt.h): plans, schedules, launches.
+//
+// A plan holds W (and W^H) in the element type, a fusion schedule -- the list
+// of passes, each applying a contiguous group of modes of Algorithm 1 in one
+// HBM round trip -- and the launch geometry of every pass.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gtt.h"
+#include "gtt_internal.h"
+#include "gtt_plan.h"
+
+using namespace gtt;
+
+static thread_local std::string g_last_error;
+
+namespace gtt {
+
+gtt_status_t set_error(gtt_status_t st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+gtt_status_t cuda_error(cudaError_t e, const char *what) {
+    return set_error(GTT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static long long ipow_ll(int b, int e) {
+    long long r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+// Build the launch description of one pass (modes [m0, m0+g), run r, window D).
+gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPlan *out) {
+    const int b = P->b, es = P->es;
+    PassPlan pp;
+    pp.m0 = m0;
+    pp.g = g;
+    pp.D = D;
+    pp.r = r;
+    const long long L = ipow_ll(b, m0), M = ipow_ll(b, g);
+    if (L % r != 0 || g < D || g < 1) return set_error(GTT_ERR_INTERNAL, "bad pass geometry");
+    if (L / r > (1ll << 31) || M * r > (1ll << 24))
+        return set_error(GTT_ERR_UNSUPPORTED, "pass geometry exceeds 32-bit tile indexing");
+    const long long tile = M * r;
+    const int RB = (int)ipow_ll(b, D);
+    PassParams &p = pp.params;
+    memset(&p, 0, sizeof(p));
+    p.total = P->total;
+    p.L = L;
+    p.tiles = P->total / tile;
+    p.r = (uint32_t)r;
+    p.M = (uint32_t)M;
+    p.tile_elems = (uint32_t)tile;
+    p.lo_blocks = (uint32_t)(L / r);
+    p.div_lo_blocks.init(p.lo_blocks);
+    p.div_r.init((uint32_t)r);
+    const int CE = 16 / es;
+    if (L == r && tile % CE == 0)
+        p.vec_mode = 1;
+    else if (r % CE == 0 && L % CE == 0)
+        p.vec_mode = 2;
+    else
+        p.vec_mode = 0;
+    p.div_cpr.init(p.vec_mode == 2 ? (uint32_t)(r / CE) : 1u);
+    // register stages: windows [s*D, s*D+D), the last slid down to [g-D, g)
+    const int S = (g + D - 1) / D;
+    if (S > kMaxStages) return set_error(GTT_ERR_INTERNAL, "too many stages");
+    p.nstages = S;
+    for (int s = 0; s < S; ++s) {
+        int a = s * D, mask = (1 << D) - 1;
+        if (a + D > g) {
+            const int first_new = a;  // digits below were applied by earlier stages
+            a = g - D;
+            mask = 0;
+            for (int k = 0; k < D; ++k)
+                if (a + k >= first_new) mask |= 1 << k;
+        }
+        p.stage_a[s] = a;
+        p.stage_mask[s] = mask;
+        p.stage_strideA[s] = (uint32_t)(r * ipow_ll(b, a));
+        p.stage_divBa[s].init((uint32_t)ipow_ll(b, a));
+    }
+    pp.kern = pass_kernel((int)P->dtype, b, D);
+    if (!pp.kern) return set_error(GTT_ERR_INTERNAL, "no kernel instantiation for (dtype, b, D)");
+    const long long nslots = tile / RB;
+    int block = (int)std::min<long long>(kPassMaxThreads, ((nslots + 31) / 32) * 32);
+    pp.block = std::max(block, 32);
+    pp.smem = (size_t)(tile + tile / RB + 1) * es;
+    pp.smem = (pp.smem + 15) / 16 * 16;
+    if (pp.smem > 227 * 1024) return set_error(GTT_ERR_INTERNAL, "tile exceeds shared memory");
+    cudaError_t e;
+    if (pp.smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(pp.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pp.kern, pp.block, pp.smem);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+    if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "pass kernel cannot be resident");
+    long long grid = (long long)per_sm * P->num_sms;
+    pp.grid = (int)std::min<long long>(grid, p.tiles);
+    pp.ctas_per_sm = per_sm;
+    *out = pp;
+    return GTT_OK;
+}
+
+// Fixed-rule schedule: greedy passes with tiles of at most max_tile_bytes and
+// runs of at least min_run_bytes (when the lower digits allow it).
+gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long min_run_bytes,
+                           std::vector<PassPlan> *out) {
+    const int b = P->b, n = P->n, es = P->es;
+    const int DM = dmax_bytes(es, b);
+    const long long tmax = std::max<long long>(max_tile_bytes / es, b);
+    std::vector<PassPlan> passes;
+    int m0 = 0;
+    while (m0 < n) {
+        long long r = 1;
+        if (m0 > 0) {
+            // r = b^j, j <= m0: smallest with r*es >= min_run_bytes, keeping b*r <= tmax
+            int j = 0;
+            while (j < m0 && r * es < min_run_bytes && r * b * b <= tmax) {
+                r *= b;
+                ++j;
+            }
+        }
+        int g = 0;
+        long long M = 1;
+        while (m0 + g < n && M * b * r <= tmax) {
+            M *= b;
+            ++g;
+        }
+        if (g == 0) g = 1;
+        const int D = g >= DM ? DM : 1;
+        PassPlan pp;
+        gtt_status_t st = build_pass(P, m0, g, r, D, &pp);
+        if (st != GTT_OK) return st;
+        passes.push_back(pp);
+        m0 += g;
+    }
+    *out = passes;
+    return GTT_OK;
+}
+
+} // namespace gtt
+
+// ------------------------------------------------------------------ C ABI
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static gtt_status_t check_device(gtt_plan_s *P) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev != P->device)
+        return set_error(GTT_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W,
+                                        gtt_dtype_t dtype, long long batch) {
+    if (!out || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL out or W");
+    *out = nullptr;
+    if (b < 2 || b > 16) return set_error(GTT_ERR_INVALID_ARG, "b must be in [2, 16]");
+    if (n < 1) return set_error(GTT_ERR_INVALID_ARG, "n must be >= 1");
+    if (batch < 1) return set_error(GTT_ERR_INVALID_ARG, "batch must be >= 1");
+    if ((int)dtype < 0 || (int)dtype > 4) return set_error(GTT_ERR_INVALID_ARG, "unknown dtype");
+    long long N = 1;
+    for (int i = 0; i < n; ++i) {
+        N *= b;
+        if (N > (1ll << 36)) return set_error(GTT_ERR_INVALID_ARG, "N = b^n above 2^36");
+    }
+    if (N > (1ll << 40) / batch) return set_error(GTT_ERR_INVALID_ARG, "batch * N above 2^40");
+    gtt_plan_s *P = new (std::nothrow) gtt_plan_s();
+    if (!P) return set_error(GTT_ERR_ALLOC, "host allocation failed");
+    P->b = b;
+    P->n = n;
+    P->dtype = dtype;
+    P->batch = batch;
+    P->N = N;
+    P->total = N * batch;
+    P->es = elem_size((int)dtype);
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_error(e, "device query");
+    }
+    const size_t wbytes = (size_t)b * b * P->es;
+    P->Wf.assign((const unsigned char *)W, (const unsigned char *)W + wbytes);
+    P->Wa.resize(wbytes);
+    // W^H: transpose, and conjugate for complex types
+    for (int i = 0; i < b; ++i)
+        for (int j = 0; j < b; ++j) {
+            unsigned char *dst = &P->Wa[((size_t)i * b + j) * P->es];
+            const unsigned char *src = &P->Wf[((size_t)j * b + i) * P->es];
+            memcpy(dst, src, P->es);
+            if (dtype == GTT_C64) {
+                float im;
+                memcpy(&im, dst + 4, 4);
+                im = -im;
+                memcpy(dst + 4, &im, 4);
+            } else if (dtype == GTT_C128) {
+                double im;
+                memcpy(&im, dst + 8, 8);
+                im = -im;
+                memcpy(dst + 8, &im, 8);
+            }
+        }
+    gtt_status_t st = make_schedule(P, kDefaultTileBytes, kDefaultRunBytes, &P->passes);
+    if (st != GTT_OK) {
+        delete P;
+        return st;
+    }
+    *out = P;
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (precision == GTT_PREC_AUTO || precision == GTT_PREC_FP32) {
+        P->precision = precision;
+        return GTT_OK;
+    }
+    if (precision == GTT_PREC_BF16X3)
+        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 precision is not available in this build");
+    return set_error(GTT_ERR_INVALID_ARG, "unknown precision");
+}
+
+extern "C" gtt_status_t gtt_plan_set_schedule(gtt_plan_t P, long long max_tile_bytes,
+                                             long long min_run_bytes) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (max_tile_bytes < 16 || max_tile_bytes > 220 * 1024 || min_run_bytes < 0 ||
+        min_run_bytes > max_tile_bytes)
+        return set_error(GTT_ERR_INVALID_ARG, "schedule limits out of range");
+    std::vector<PassPlan> passes;
+    gtt_status_t st = make_schedule(P, max_tile_bytes, min_run_bytes, &passes);
+    if (st != GTT_OK) return st;
+    P->passes = passes;
+    return GTT_OK;
+}
+
+namespace gtt {
+// Launch every pass of the schedule with the given W bytes.
+gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
+                        cudaStream_t stream) {
+    for (size_t i = 0; i < P->passes.size(); ++i) {
+        PassPlan &pp = P->passes[i];
+        const void *in = i == 0 ? x : (const void *)y;
+        void *outp = y;
+        void *args[4] = {(void *)&in, (void *)&outp, (void *)&pp.params, (void *)Wb.data()};
+        cudaError_t e = cudaLaunchKernel(pp.kern, dim3(pp.grid), dim3(pp.block), args, pp.smem, stream);
+        if (e != cudaSuccess) return cuda_error(e, "pass kernel launch");
+    }
+    return GTT_OK;
+}
+} // namespace gtt
+
+static gtt_status_t transform(gtt_plan_t P, const void *x, void *y, gtt_stream_t stream, bool adjoint) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (!x || !y) return set_error(GTT_ERR_INVALID_ARG, "NULL data pointer");
+    if (!aligned16(x) || !aligned16(y)) return set_error(GTT_ERR_INVALID_ARG, "data pointers must be 16-byte aligned");
+    gtt_status_t st = check_device(P);
+    if (st != GTT_OK) return st;
+    return run_passes(P, adjoint ? P->Wa : P->Wf, x, y, (cudaStream_t)stream);
+}
+
+extern "C" gtt_status_t gtt_forward(gtt_plan_t P, const void *x, void *y, gtt_stream_t stream) {
+    return transform(P, x, y, stream, false);
+}
+
+extern "C" gtt_status_t gtt_inverse(gtt_plan_t P, const void *y, void *x, gtt_stream_t stream) {
+    return transform(P, y, x, stream, true);
+}
+
+static gtt_status_t transform_host(gtt_plan_t P, const void *xh, void *yh, gtt_stream_t stream,
+                                   bool adjoint) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (!xh || !yh) return set_error(GTT_ERR_INVALID_ARG, "NULL host pointer");
+    gtt_status_t st = check_device(P);
+    if (st != GTT_OK) return st;
+    const size_t bytes = (size_t)P->total * P->es;
+    if (!P->dstage) {
+        cudaError_t e = cudaMalloc(&P->dstage, bytes);
+        if (e != cudaSuccess) {
+            P->dstage = nullptr;
+            return set_error(GTT_ERR_ALLOC, std::string("staging buffer: ") + cudaGetErrorString(e));
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(P->dstage, xh, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "host to device copy");
+    st = run_passes(P, adjoint ? P->Wa : P->Wf, P->dstage, P->dstage, s);
+    if (st != GTT_OK) return st;
+    e = cudaMemcpyAsync(yh, P->dstage, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_error(e, "device to host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "stream synchronize");
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_forward_host(gtt_plan_t P, const void *x, void *y, gtt_stream_t s) {
+    return transform_host(P, x, y, s, false);
+}
+
+extern "C" gtt_status_t gtt_inverse_host(gtt_plan_t P, const void *y, void *x, gtt_stream_t s) {
+    return transform_host(P, y, x, s, true);
+}
+
+extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
+    if (!P || !buf || len == 0) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or buffer");
+    std::string s = "{\"b\": " + std::to_string(P->b) + ", \"n\": " + std::to_string(P->n) +
+                    ", \"dtype\": " + std::to_string((int)P->dtype) + ", \"batch\": " +
+                    std::to_string(P->batch) + ", \"launches_per_transform\": " +
+                    std::to_string(P->passes.size()) + ", \"passes\": [";
+    for (size_t i = 0; i < P->passes.size(); ++i) {
+        const PassPlan &pp = P->passes[i];
+        char tmp[320];
+        snprintf(tmp, sizeof tmp,
+                 "%s{\"m0\": %d, \"g\": %d, \"r\": %lld, \"D\": %d, \"tile_bytes\": %lld, "
+                 "\"tiles\": %lld, \"grid\": %d, \"block\": %d, \"smem\": %zu, \"ctas_per_sm\": %d, "
+                 "\"vec_mode\": %d}",
+                 i ? ", " : "", pp.m0, pp.g, pp.r, pp.D, (long long)pp.params.tile_elems * P->es,
+                 pp.params.tiles, pp.grid, pp.block, pp.smem, pp.ctas_per_sm, pp.params.vec_mode);
+        s += tmp;
+    }
+    s += "]}";
+    snprintf(buf, len, "%s", s.c_str());
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
+    if (!P) return GTT_OK;
+    if (P->dstage) cudaFree(P->dstage);
+    delete P;
+    return GTT_OK;
+}
+
+extern "C" const char *gtt_last_error(void) { return g_last_error.c_str(); }

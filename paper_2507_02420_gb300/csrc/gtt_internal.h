@@ -1,0 +1,47 @@
+// Internal interface between the C-ABI layer and the kernel translation units.
+#pragma once
+#include "gtt_pass.cuh"
+
+namespace gtt {
+
+// dtype codes follow gtt_dtype_t: 0 F64, 1 F32, 2 C64, 3 C128, 4 I32.
+inline int elem_size(int dtype) {
+    switch (dtype) {
+    case 0: return 8;
+    case 1: return 4;
+    case 2: return 8;
+    case 3: return 16;
+    case 4: return 4;
+    default: return 0;
+    }
+}
+
+// Register-window depth D of the pass kernel: the largest D with B^D elements
+// of the type fitting a ~32-register budget (B^D <= 32 for 4-byte types,
+// <= 16 for 8-byte types, <= 9 for 16-byte types).
+__host__ __device__ constexpr int dmax_bytes(int es, int b) {
+    return es == 4 ? (b == 2 ? 5 : b == 3 ? 3 : (b == 4 || b == 5) ? 2 : 1)
+         : es == 8 ? (b == 2 ? 4 : (b == 3 || b == 4) ? 2 : 1)
+                   : (b == 2 ? 3 : b == 3 ? 2 : 1);
+}
+
+// Kernel entry for (dtype, b, D); D must be 1 or dmax_bytes(es, b).  nullptr
+// if no such instantiation exists.
+const void *pass_kernel_f64(int b, int d);
+const void *pass_kernel_f32(int b, int d);
+const void *pass_kernel_c64(int b, int d);
+const void *pass_kernel_c128(int b, int d);
+const void *pass_kernel_u32(int b, int d);
+
+inline const void *pass_kernel(int dtype, int b, int d) {
+    switch (dtype) {
+    case 0: return pass_kernel_f64(b, d);
+    case 1: return pass_kernel_f32(b, d);
+    case 2: return pass_kernel_c64(b, d);
+    case 3: return pass_kernel_c128(b, d);
+    case 4: return pass_kernel_u32(b, d);
+    default: return nullptr;
+    }
+}
+
+} // namespace gtt

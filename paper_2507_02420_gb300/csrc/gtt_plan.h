@@ -1,0 +1,49 @@
+// Plan object and host-side helpers shared by the C-ABI translation units.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/gtt.h"
+#include "gtt_internal.h"
+
+namespace gtt {
+
+// Default fixed-rule schedule: tiles of at most this many bytes (several CTAs
+// per SM) and runs of at least this many contiguous bytes in strided passes.
+constexpr long long kDefaultTileBytes = 48 * 1024;
+constexpr long long kDefaultRunBytes = 128;
+
+// One pass of a schedule: modes [m0, m0+g) with runs of r elements, register
+// windows of D digits, and its launch geometry.
+struct PassPlan {
+    int m0 = 0, g = 0, D = 1;
+    long long r = 1;
+    PassParams params;
+    const void *kern = nullptr;
+    int grid = 0, block = 0, ctas_per_sm = 0;
+    size_t smem = 0;
+};
+
+gtt_status_t set_error(gtt_status_t st, const std::string &msg);
+gtt_status_t cuda_error(cudaError_t e, const char *what);
+
+} // namespace gtt
+
+struct gtt_plan_s {
+    int device = 0, num_sms = 0;
+    int b = 0, n = 0, es = 0;
+    gtt_dtype_t dtype = GTT_F32;
+    long long batch = 0, N = 0, total = 0;
+    int precision = GTT_PREC_AUTO;
+    std::vector<unsigned char> Wf, Wa;  // W and W^H in the element type, row-major
+    std::vector<gtt::PassPlan> passes;  // forward/inverse schedule
+    void *dstage = nullptr;             // device staging for the host-buffer calls
+};
+
+namespace gtt {
+gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPlan *out);
+gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long min_run_bytes,
+                           std::vector<PassPlan> *out);
+gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
+                        cudaStream_t stream);
+} // namespace gtt
