@@ -158,6 +158,16 @@ gtt_status_t gtt_inverse_host(gtt_plan_t plan, const void *y_host, void *x_host,
  */
 gtt_status_t gtt_plan_describe(gtt_plan_t plan, char *buf, size_t len);
 
+/*
+ * gtt_plan_set_timing -- when enable != 0, every kernel the plan launches is
+ * bracketed by two CUDA events recorded on the launch stream.
+ * gtt_plan_timing -- wait for the recorded events and write, as one line of
+ * JSON, per kernel: its name, number of launches and summed device time (ms)
+ * since the previous gtt_plan_timing call; then forget the records.
+ */
+gtt_status_t gtt_plan_set_timing(gtt_plan_t plan, int enable);
+gtt_status_t gtt_plan_timing(gtt_plan_t plan, char *buf, size_t len);
+
 /* Release the plan and everything it owns.  NULL is accepted. */
 gtt_status_t gtt_plan_destroy(gtt_plan_t plan);
 

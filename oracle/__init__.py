@@ -69,6 +69,7 @@ def _load():
             "oracle_modes_c": [I, I, P, LL, P, P, I],
             "oracle_modes_r": [I, I, P, LL, P, P, I],
             "oracle_modes_u32": [I, I, P, LL, P, P, I],
+            "oracle_mode_pass_c": [I, I, P, I, P, P, I],
             "oracle_adjoint_c": [I, I, P, LL, P, P, I],
             "oracle_adjoint_r": [I, I, P, LL, P, P, I],
             "oracle_grad_c": [I, I, P, LL, P, P, P, P, I],
@@ -163,6 +164,17 @@ def modes(W, x, threads: int | None = None) -> np.ndarray:
     y = np.empty_like(x)
     fn = _load().oracle_modes_r if real else _load().oracle_modes_c
     _check(fn(b, n, _ptr(W), _batched(x, b ** n), _ptr(x), _ptr(y), threads), "modes")
+    return y
+
+
+def mode_pass(W, x, k: int, out=None, threads: int | None = None) -> np.ndarray:
+    """One mode-k pass (W applied to digit k) of a single complex vector."""
+    threads = default_threads() if threads is None else threads
+    W = np.ascontiguousarray(W, dtype=np.complex128)
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    b, n = _nb(W, x.shape[-1])
+    y = np.empty_like(x) if out is None else out
+    _check(_load().oracle_mode_pass_c(b, n, _ptr(W), int(k), _ptr(x), _ptr(y), threads), "mode_pass")
     return y
 
 

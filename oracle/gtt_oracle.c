@@ -296,6 +296,14 @@ int oracle_modes_u32(int b, int n, const uint32_t *W, long long batch, const uin
     return modes_generic(KIND_U, b, n, W, batch, x, y, threads);
 }
 
+/* One mode-k pass (complex) of one length-N vector, in -> out (distinct). */
+int oracle_mode_pass_c(int b, int n, const double *W, int k, const double *x, double *y,
+                       int threads) {
+    if (k < 0 || k >= n) return -1;
+    mode_pass(KIND_C, b, W, ipow(b, n), k, x, y, threads);
+    return 0;
+}
+
 /* W^H (conjugate transpose) of a complex b x b matrix. */
 static void adjoint_of(int b, const cplx *W, cplx *WH) {
     for (int i = 0; i < b; ++i)

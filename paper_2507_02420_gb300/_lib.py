@@ -28,6 +28,8 @@ SIGNATURES = {
     "gtt_forward_host": (_I, [_P, _P, _P, _P]),
     "gtt_inverse_host": (_I, [_P, _P, _P, _P]),
     "gtt_plan_describe": (_I, [_P, ctypes.c_char_p, _S]),
+    "gtt_plan_set_timing": (_I, [_P, _I]),
+    "gtt_plan_timing": (_I, [_P, ctypes.c_char_p, _S]),
     "gtt_plan_destroy": (_I, [_P]),
     "gtt_last_error": (ctypes.c_char_p, []),
 }

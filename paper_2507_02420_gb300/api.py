@@ -95,6 +95,15 @@ class Plan:
         check(self._lib.gtt_plan_describe(self._h, buf, len(buf)), "gtt_plan_describe")
         return json.loads(buf.value.decode())
 
+    def set_timing(self, enable: bool):
+        check(self._lib.gtt_plan_set_timing(self._h, int(bool(enable))), "gtt_plan_set_timing")
+
+    def timing(self) -> dict:
+        """Per-kernel launches and summed device ms since the last call (waits)."""
+        buf = ctypes.create_string_buffer(65536)
+        check(self._lib.gtt_plan_timing(self._h, buf, len(buf)), "gtt_plan_timing")
+        return json.loads(buf.value.decode())
+
     # ---------------------------------------------------------- device calls
     def _check_dev(self, t: torch.Tensor, name: str):
         if not isinstance(t, torch.Tensor) or not t.is_cuda:

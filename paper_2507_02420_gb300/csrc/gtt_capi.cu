@@ -106,6 +106,9 @@ gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPl
     long long grid = (long long)per_sm * P->num_sms;
     pp.grid = (int)std::min<long long>(grid, p.tiles);
     pp.ctas_per_sm = per_sm;
+    static const char *tnames[] = {"f64", "f32", "c64", "c128", "u32"};
+    pp.name = std::string("gtt_pass_kernel<") + tnames[(int)P->dtype] + "," + std::to_string(b) +
+              "," + std::to_string(D) + ">";
     *out = pp;
     return GTT_OK;
 }
@@ -136,6 +139,12 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
             ++g;
         }
         if (g == 0) g = 1;
+        if (m0 > 0) {
+            // all remaining digits fit: widen the run to fill the tile
+            long long L = 1;
+            for (int i = 0; i < m0; ++i) L *= b;
+            while (m0 + g == n && r * b <= L && M * r * b <= tmax) r *= b;
+        }
         const int D = g >= DM ? DM : 1;
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, D, &pp);
@@ -246,6 +255,35 @@ extern "C" gtt_status_t gtt_plan_set_schedule(gtt_plan_t P, long long max_tile_b
 }
 
 namespace gtt {
+static cudaError_t pool_event(gtt_plan_s *P, cudaEvent_t *ev) {
+    if (!P->event_pool.empty()) {
+        *ev = P->event_pool.back();
+        P->event_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(ev);
+}
+
+gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block, void **args,
+                          size_t smem, cudaStream_t stream, const std::string &name) {
+    TimingRecord rec;
+    if (P->timing) {
+        cudaError_t e = pool_event(P, &rec.start);
+        if (e == cudaSuccess) e = pool_event(P, &rec.stop);
+        if (e == cudaSuccess) e = cudaEventRecord(rec.start, stream);
+        if (e != cudaSuccess) return cuda_error(e, "timing event");
+    }
+    cudaError_t e = cudaLaunchKernel(kern, grid, block, args, smem, stream);
+    if (e != cudaSuccess) return cuda_error(e, "kernel launch");
+    if (P->timing) {
+        e = cudaEventRecord(rec.stop, stream);
+        if (e != cudaSuccess) return cuda_error(e, "timing event");
+        rec.name = name;
+        P->pending.push_back(rec);
+    }
+    return GTT_OK;
+}
+
 // Launch every pass of the schedule with the given W bytes.
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream) {
@@ -254,12 +292,55 @@ gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, con
         const void *in = i == 0 ? x : (const void *)y;
         void *outp = y;
         void *args[4] = {(void *)&in, (void *)&outp, (void *)&pp.params, (void *)Wb.data()};
-        cudaError_t e = cudaLaunchKernel(pp.kern, dim3(pp.grid), dim3(pp.block), args, pp.smem, stream);
-        if (e != cudaSuccess) return cuda_error(e, "pass kernel launch");
+        gtt_status_t st = launch_timed(P, pp.kern, dim3(pp.grid), dim3(pp.block), args, pp.smem,
+                                       stream, pp.name);
+        if (st != GTT_OK) return st;
     }
     return GTT_OK;
 }
 } // namespace gtt
+
+extern "C" gtt_status_t gtt_plan_set_timing(gtt_plan_t P, int enable) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    P->timing = enable != 0;
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_plan_timing(gtt_plan_t P, char *buf, size_t len) {
+    if (!P || !buf || len == 0) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or buffer");
+    std::vector<std::string> names;
+    std::vector<long long> counts;
+    std::vector<double> total;
+    gtt_status_t st = GTT_OK;
+    for (TimingRecord &r : P->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (e != cudaSuccess && st == GTT_OK) st = cuda_error(e, "timing readback");
+        size_t k = 0;
+        while (k < names.size() && names[k] != r.name) ++k;
+        if (k == names.size()) {
+            names.push_back(r.name);
+            counts.push_back(0);
+            total.push_back(0.0);
+        }
+        counts[k] += 1;
+        total[k] += ms;
+        P->event_pool.push_back(r.start);
+        P->event_pool.push_back(r.stop);
+    }
+    P->pending.clear();
+    std::string s = "{\"kernels\": [";
+    for (size_t k = 0; k < names.size(); ++k) {
+        char tmp[256];
+        snprintf(tmp, sizeof tmp, "%s{\"name\": \"%s\", \"launches\": %lld, \"total_ms\": %.6f}",
+                 k ? ", " : "", names[k].c_str(), counts[k], total[k]);
+        s += tmp;
+    }
+    s += "]}";
+    snprintf(buf, len, "%s", s.c_str());
+    return st;
+}
 
 static gtt_status_t transform(gtt_plan_t P, const void *x, void *y, gtt_stream_t stream, bool adjoint) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
@@ -320,13 +401,14 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                     std::to_string(P->passes.size()) + ", \"passes\": [";
     for (size_t i = 0; i < P->passes.size(); ++i) {
         const PassPlan &pp = P->passes[i];
-        char tmp[320];
+        char tmp[400];
         snprintf(tmp, sizeof tmp,
-                 "%s{\"m0\": %d, \"g\": %d, \"r\": %lld, \"D\": %d, \"tile_bytes\": %lld, "
-                 "\"tiles\": %lld, \"grid\": %d, \"block\": %d, \"smem\": %zu, \"ctas_per_sm\": %d, "
-                 "\"vec_mode\": %d}",
-                 i ? ", " : "", pp.m0, pp.g, pp.r, pp.D, (long long)pp.params.tile_elems * P->es,
-                 pp.params.tiles, pp.grid, pp.block, pp.smem, pp.ctas_per_sm, pp.params.vec_mode);
+                 "%s{\"kernel\": \"%s\", \"m0\": %d, \"g\": %d, \"r\": %lld, \"D\": %d, "
+                 "\"tile_bytes\": %lld, \"tiles\": %lld, \"grid\": %d, \"block\": %d, \"smem\": %zu, "
+                 "\"ctas_per_sm\": %d, \"vec_mode\": %d}",
+                 i ? ", " : "", pp.name.c_str(), pp.m0, pp.g, pp.r, pp.D,
+                 (long long)pp.params.tile_elems * P->es, pp.params.tiles, pp.grid, pp.block, pp.smem,
+                 pp.ctas_per_sm, pp.params.vec_mode);
         s += tmp;
     }
     s += "]}";
@@ -337,6 +419,11 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
 extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
     if (!P) return GTT_OK;
     if (P->dstage) cudaFree(P->dstage);
+    for (TimingRecord &r : P->pending) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (cudaEvent_t ev : P->event_pool) cudaEventDestroy(ev);
     delete P;
     return GTT_OK;
 }

@@ -22,6 +22,13 @@ struct PassPlan {
     const void *kern = nullptr;
     int grid = 0, block = 0, ctas_per_sm = 0;
     size_t smem = 0;
+    std::string name;  // kernel name with its template arguments
+};
+
+// Launch timing: event pairs recorded around each launch when enabled.
+struct TimingRecord {
+    cudaEvent_t start, stop;
+    std::string name;
 };
 
 gtt_status_t set_error(gtt_status_t st, const std::string &msg);
@@ -38,12 +45,18 @@ struct gtt_plan_s {
     std::vector<unsigned char> Wf, Wa;  // W and W^H in the element type, row-major
     std::vector<gtt::PassPlan> passes;  // forward/inverse schedule
     void *dstage = nullptr;             // device staging for the host-buffer calls
+    bool timing = false;
+    std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace gtt {
 gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPlan *out);
 gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long min_run_bytes,
                            std::vector<PassPlan> *out);
+// Launch `kern` with `args`, recording timing events when the plan asks for it.
+gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block, void **args,
+                          size_t smem, cudaStream_t stream, const std::string &name);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
 } // namespace gtt
