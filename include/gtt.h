@@ -91,6 +91,11 @@ typedef enum {
 gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_dtype_t dtype,
                              long long batch);
 
+/* Replace the plan's base matrix (HOST pointer, same layout and type as in
+ * gtt_plan_create) without rebuilding its schedule; used when W is trained.
+ * Calls already queued on a stream keep the W they were launched with. */
+gtt_status_t gtt_plan_set_w(gtt_plan_t plan, const void *W);
+
 /* Select the arithmetic of the b = 16 contraction (gtt_precision_t).  Other b
  * accept GTT_PREC_AUTO and GTT_PREC_FP32 only.  GTT_PREC_BF16X3 requires b = 16
  * and dtype F32; otherwise GTT_ERR_UNSUPPORTED. */

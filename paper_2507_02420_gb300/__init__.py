@@ -8,3 +8,4 @@ include/gtt.h (libgtt.so); this package is its thin Python binding.
 from .api import (C64, C128, F32, F64, I32, PREC_AUTO, PREC_BF16X3, PREC_FP32, Plan,  # noqa: F401
                   dtype_code)
 from ._lib import GTTError, LIB_PATH, load  # noqa: F401
+from .autograd import GTTFunction, gtt  # noqa: F401

@@ -83,6 +83,14 @@ class Plan:
         except Exception:
             pass
 
+    def set_w(self, W):
+        """Replace W (host copy taken now) without rebuilding the schedule."""
+        Wn = W.detach().cpu().numpy() if isinstance(W, torch.Tensor) else np.asarray(W)
+        if Wn.shape != (self.b, self.b):
+            raise ValueError("W shape differs from the plan's")
+        self._W = _w_host_bytes(Wn, self.dtype)
+        check(self._lib.gtt_plan_set_w(self._h, self._W.ctypes.data_as(ctypes.c_void_p)), "gtt_plan_set_w")
+
     def set_precision(self, prec: int):
         check(self._lib.gtt_plan_set_precision(self._h, int(prec)), "gtt_plan_set_precision")
 

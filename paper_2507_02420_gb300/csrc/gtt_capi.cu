@@ -96,7 +96,7 @@ gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPl
     if (pp.smem > 227 * 1024) return set_error(GTT_ERR_INTERNAL, "tile exceeds shared memory");
     cudaError_t e;
     if (pp.smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(pp.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem);
+        e = allow_max_smem(pp.kern, P->smem_optin);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
     }
     int per_sm = 0;
@@ -160,6 +160,38 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 
 // ------------------------------------------------------------------ C ABI
 
+// Copy W (host, element type) into the plan and derive W^H (the transpose,
+// conjugated for complex types).
+static void set_w_bytes(gtt_plan_s *P, const void *W) {
+    const int b = P->b, es = P->es;
+    const size_t wbytes = (size_t)b * b * es;
+    P->Wf.assign((const unsigned char *)W, (const unsigned char *)W + wbytes);
+    P->Wa.resize(wbytes);
+    for (int i = 0; i < b; ++i)
+        for (int j = 0; j < b; ++j) {
+            unsigned char *dst = &P->Wa[((size_t)i * b + j) * es];
+            const unsigned char *src = &P->Wf[((size_t)j * b + i) * es];
+            memcpy(dst, src, es);
+            if (P->dtype == GTT_C64) {
+                float im;
+                memcpy(&im, dst + 4, 4);
+                im = -im;
+                memcpy(dst + 4, &im, 4);
+            } else if (P->dtype == GTT_C128) {
+                double im;
+                memcpy(&im, dst + 8, 8);
+                im = -im;
+                memcpy(dst + 8, &im, 8);
+            }
+        }
+}
+
+extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
+    if (!P || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or W");
+    set_w_bytes(P, W);
+    return GTT_OK;
+}
+
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 static gtt_status_t check_device(gtt_plan_s *P) {
@@ -196,31 +228,15 @@ extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const voi
     P->es = elem_size((int)dtype);
     cudaError_t e = cudaGetDevice(&P->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&P->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     if (e != cudaSuccess) {
         delete P;
         return cuda_error(e, "device query");
     }
     const size_t wbytes = (size_t)b * b * P->es;
-    P->Wf.assign((const unsigned char *)W, (const unsigned char *)W + wbytes);
-    P->Wa.resize(wbytes);
-    // W^H: transpose, and conjugate for complex types
-    for (int i = 0; i < b; ++i)
-        for (int j = 0; j < b; ++j) {
-            unsigned char *dst = &P->Wa[((size_t)i * b + j) * P->es];
-            const unsigned char *src = &P->Wf[((size_t)j * b + i) * P->es];
-            memcpy(dst, src, P->es);
-            if (dtype == GTT_C64) {
-                float im;
-                memcpy(&im, dst + 4, 4);
-                im = -im;
-                memcpy(dst + 4, &im, 4);
-            } else if (dtype == GTT_C128) {
-                double im;
-                memcpy(&im, dst + 8, 8);
-                im = -im;
-                memcpy(dst + 8, &im, 8);
-            }
-        }
+    (void)wbytes;
+    set_w_bytes(P, W);
     gtt_status_t st = make_schedule(P, kDefaultTileBytes, kDefaultRunBytes, &P->passes);
     if (st != GTT_OK) {
         delete P;
@@ -419,6 +435,9 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
 extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
     if (!P) return GTT_OK;
     if (P->dstage) cudaFree(P->dstage);
+    if (P->ws_grad) cudaFree(P->ws_grad);
+    if (P->ws_ck) cudaFree(P->ws_ck);
+    if (P->ws_dw) cudaFree(P->ws_dw);
     for (TimingRecord &r : P->pending) {
         cudaEventDestroy(r.start);
         cudaEventDestroy(r.stop);

@@ -45,3 +45,41 @@ inline const void *pass_kernel(int dtype, int b, int d) {
 }
 
 } // namespace gtt
+
+namespace gtt {
+// Backward pass kernels and the dW reduction (floating-point types only).
+const void *bwd_kernel_f64(int b);
+const void *bwd_kernel_f32(int b);
+const void *bwd_kernel_c64(int b);
+const void *bwd_kernel_c128(int b);
+const void *dw_reduce_kernel_f64();
+const void *dw_reduce_kernel_f32();
+const void *dw_reduce_kernel_c64();
+const void *dw_reduce_kernel_c128();
+
+inline const void *bwd_kernel(int dtype, int b) {
+    switch (dtype) {
+    case 0: return bwd_kernel_f64(b);
+    case 1: return bwd_kernel_f32(b);
+    case 2: return bwd_kernel_c64(b);
+    case 3: return bwd_kernel_c128(b);
+    default: return nullptr;
+    }
+}
+inline const void *dw_reduce_kernel(int dtype) {
+    switch (dtype) {
+    case 0: return dw_reduce_kernel_f64();
+    case 1: return dw_reduce_kernel_f32();
+    case 2: return dw_reduce_kernel_c64();
+    case 3: return dw_reduce_kernel_c128();
+    default: return nullptr;
+    }
+}
+// rows of dW per backward thread (mirrors bwd_rows in gtt_bwd.cuh)
+inline int bwd_rows_host(int b, bool cplx) {
+    int budget = cplx ? 32 : 64;
+    int R = b;
+    while (R * b > budget && R % 2 == 0) R /= 2;
+    return R;
+}
+} // namespace gtt

@@ -25,11 +25,28 @@ struct PassPlan {
     std::string name;  // kernel name with its template arguments
 };
 
+// One pass of the backward schedule: the tile geometry (one stage per digit),
+// the matching forward pass used to recompute checkpoints, and the launch.
+struct BwdPass {
+    PassPlan geo, fwd;
+    const void *kern = nullptr;
+    int grid = 0, g = 0;
+    size_t smem = 0;
+    std::string name;
+};
+constexpr size_t kBwdSmemBudget = 100 * 1024;
+
 // Launch timing: event pairs recorded around each launch when enabled.
 struct TimingRecord {
     cudaEvent_t start, stop;
     std::string name;
 };
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// (one limit per kernel, so passes of different tile sizes can share it).
+inline cudaError_t allow_max_smem(const void *kern, int optin) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
 
 gtt_status_t set_error(gtt_status_t st, const std::string &msg);
 gtt_status_t cuda_error(cudaError_t e, const char *what);
@@ -37,7 +54,7 @@ gtt_status_t cuda_error(cudaError_t e, const char *what);
 } // namespace gtt
 
 struct gtt_plan_s {
-    int device = 0, num_sms = 0;
+    int device = 0, num_sms = 0, smem_optin = 0;
     int b = 0, n = 0, es = 0;
     gtt_dtype_t dtype = GTT_F32;
     long long batch = 0, N = 0, total = 0;
@@ -45,6 +62,10 @@ struct gtt_plan_s {
     std::vector<unsigned char> Wf, Wa;  // W and W^H in the element type, row-major
     std::vector<gtt::PassPlan> passes;  // forward/inverse schedule
     void *dstage = nullptr;             // device staging for the host-buffer calls
+    std::vector<gtt::BwdPass> bwd;       // backward schedule (built on first use)
+    bool bwd_ready = false;
+    void *ws_grad = nullptr, *ws_ck = nullptr, *ws_dw = nullptr;  // backward workspace
+    size_t ws_grad_bytes = 0, ws_ck_bytes = 0, ws_dw_bytes = 0;
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
     std::vector<cudaEvent_t> event_pool;
@@ -57,6 +78,7 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 // Launch `kern` with `args`, recording timing events when the plan asks for it.
 gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block, void **args,
                           size_t smem, cudaStream_t stream, const std::string &name);
+gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
 } // namespace gtt

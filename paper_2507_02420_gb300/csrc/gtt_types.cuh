@@ -78,6 +78,12 @@ __device__ __forceinline__ c128 fma_acc(c128 w, c128 v, c128 acc) {
     return acc;
 }
 
+// a + b
+__device__ __forceinline__ float add_(float a, float b) { return a + b; }
+__device__ __forceinline__ double add_(double a, double b) { return a + b; }
+__device__ __forceinline__ c64 add_(c64 a, c64 b) { return c64{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ c128 add_(c128 a, c128 b) { return c128{a.re + b.re, a.im + b.im}; }
+
 // Compile-time integer power.
 __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 
