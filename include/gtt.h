@@ -145,6 +145,30 @@ gtt_status_t gtt_backward(gtt_plan_t plan, const void *x_saved, const void *dy, 
                           gtt_stream_t stream);
 
 /*
+ * gtt_backward_noalloc -- the same results as gtt_backward, computed without
+ * allocating any device memory (the paper has no counterpart to this call).
+ * For callers that must not allocate on the device from inside the library:
+ * code running under a framework's caching allocator that has already
+ * reserved the device's memory (where a stray cudaMalloc can fail or fragment
+ * the pool), or latency-critical loops where cudaMalloc/cudaFree would
+ * synchronize the device.
+ *   x, dy, dW as in gtt_backward.  dx is required (non-NULL) and must not
+ *   alias dy: it also holds the checkpoint between the two backward passes.
+ * Scratch: the dW partials live in a fixed 2 MiB array in the library's
+ * device globals (held by every GPU that loads the library until exit).  The
+ * first call on a device looks up that array's device address (with the
+ * plan's device current) and builds the plan's backward schedule on the host;
+ * make that first call before any stream capture.  All calls share the
+ * array and each overwrites what it reads; calls whose kernels overlap on the
+ * GPU (other streams, other plans) race on it and must be serialised.
+ * Errors: GTT_ERR_INVALID_ARG when dx is NULL or aliases dy, when the
+ * transform needs more than two backward passes (a data-sized checkpoint),
+ * or when its dW partials exceed the 2 MiB array; otherwise as gtt_backward.
+ */
+gtt_status_t gtt_backward_noalloc(gtt_plan_t plan, const void *x_saved, const void *dy, void *dx,
+                                  void *dW, gtt_stream_t stream);
+
+/*
  * gtt_forward_host / gtt_inverse_host -- the same transforms on HOST buffers:
  * copy x (batch*N elements) to plan-owned device memory, transform, copy the
  * result back into y, and wait for `stream`.  Host buffers may be pageable;

@@ -26,6 +26,7 @@ SIGNATURES = {
     "gtt_forward": (_I, [_P, _P, _P, _P]),
     "gtt_inverse": (_I, [_P, _P, _P, _P]),
     "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),
+    "gtt_backward_noalloc": (_I, [_P, _P, _P, _P, _P, _P]),
     "gtt_forward_host": (_I, [_P, _P, _P, _P]),
     "gtt_inverse_host": (_I, [_P, _P, _P, _P]),
     "gtt_plan_describe": (_I, [_P, ctypes.c_char_p, _S]),
