@@ -113,6 +113,24 @@ gtt_status_t gtt_plan_set_schedule(gtt_plan_t plan, long long max_tile_bytes,
                                    long long min_run_bytes);
 
 /*
+ * gtt_plan_set_pipeline -- choose how the forward/inverse passes stage their
+ * tiles: use_tma != 0 streams tiles through `nbuf` (1..4) shared-memory
+ * buffers with tensor-memory-accelerator copies where the tile geometry allows
+ * (b a power of two, 128-byte rows); use_tma == 0 uses plain loads and stores.
+ * Rebuilds the schedule with the current limits.  Default: use_tma = 1,
+ * nbuf = 2.  Errors: GTT_ERR_INVALID_ARG (nbuf out of range), GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_plan_set_pipeline(gtt_plan_t plan, int use_tma, int nbuf);
+
+/*
+ * gtt_plan_check -- wait for the device and report whether any kernel of this
+ * plan gave up a bounded wait (GTT_ERR_TIMEOUT; the flag is then cleared).
+ * Kernels never spin without limit: an expired wait records the error, drains
+ * the kernel's own copies and returns.
+ */
+gtt_status_t gtt_plan_check(gtt_plan_t plan);
+
+/*
  * gtt_forward -- y = G_N x for each of the plan's `batch` vectors, natural
  * ordering (Sec. 2.6 element form; Sec. 3 fast algorithm).
  *   x  device, batch*N elements (read).   y  device, batch*N elements (written).

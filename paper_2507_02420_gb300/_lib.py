@@ -23,6 +23,8 @@ SIGNATURES = {
     "gtt_plan_set_precision": (_I, [_P, _I]),
     "gtt_plan_set_w": (_I, [_P, _P]),
     "gtt_plan_set_schedule": (_I, [_P, _LL, _LL]),
+    "gtt_plan_set_pipeline": (_I, [_P, _I, _I]),
+    "gtt_plan_check": (_I, [_P]),
     "gtt_forward": (_I, [_P, _P, _P, _P]),
     "gtt_inverse": (_I, [_P, _P, _P, _P]),
     "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),

@@ -98,6 +98,14 @@ class Plan:
         check(self._lib.gtt_plan_set_schedule(self._h, int(max_tile_bytes), int(min_run_bytes)),
               "gtt_plan_set_schedule")
 
+    def set_pipeline(self, use_tma: bool = True, nbuf: int = 2):
+        check(self._lib.gtt_plan_set_pipeline(self._h, int(bool(use_tma)), int(nbuf)),
+              "gtt_plan_set_pipeline")
+
+    def check(self):
+        """Raise GTTError(GTT_ERR_TIMEOUT) if a kernel of this plan gave up a bounded wait."""
+        check(self._lib.gtt_plan_check(self._h), "gtt_plan_check")
+
     def describe(self) -> dict:
         buf = ctypes.create_string_buffer(16384)
         check(self._lib.gtt_plan_describe(self._h, buf, len(buf)), "gtt_plan_describe")

@@ -149,6 +149,7 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, D, &pp);
         if (st != GTT_OK) return st;
+        if (P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
         passes.push_back(pp);
         m0 += g;
     }
@@ -160,8 +161,44 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 
 // ------------------------------------------------------------------ C ABI
 
+// Extend a row-major b x b matrix (element layout) to the kernels' parameter
+// layout WMat<T, B>: complex64 appends the pairs (re, re) and (-im, im) of
+// every entry; FP32 appends the row pairs (W[2i][j], W[2i+1][j]) (a single
+// unused pair for odd b); other types use the element layout as it is.
+static void append_packed_pairs(gtt_plan_s *P, std::vector<unsigned char> *Wv) {
+    const int b = P->b;
+    if (P->dtype == GTT_C64) {
+        std::vector<float> ex;
+        const float *w = reinterpret_cast<const float *>(Wv->data());
+        for (int k = 0; k < b * b; ++k) {
+            ex.push_back(w[2 * k]);
+            ex.push_back(w[2 * k]);
+        }
+        for (int k = 0; k < b * b; ++k) {
+            ex.push_back(-w[2 * k + 1]);
+            ex.push_back(w[2 * k + 1]);
+        }
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(ex.data());
+        Wv->insert(Wv->end(), p, p + ex.size() * sizeof(float));
+    } else if (P->dtype == GTT_F32) {
+        std::vector<float> ex;
+        const float *w = reinterpret_cast<const float *>(Wv->data());
+        if (b % 2 == 0) {
+            for (int ip = 0; ip < b / 2; ++ip)
+                for (int j = 0; j < b; ++j) {
+                    ex.push_back(w[(2 * ip) * b + j]);
+                    ex.push_back(w[(2 * ip + 1) * b + j]);
+                }
+        } else {
+            ex.assign(2, 0.f);
+        }
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(ex.data());
+        Wv->insert(Wv->end(), p, p + ex.size() * sizeof(float));
+    }
+}
+
 // Copy W (host, element type) into the plan and derive W^H (the transpose,
-// conjugated for complex types).
+// conjugated for complex types), both in the kernels' parameter layout.
 static void set_w_bytes(gtt_plan_s *P, const void *W) {
     const int b = P->b, es = P->es;
     const size_t wbytes = (size_t)b * b * es;
@@ -184,6 +221,8 @@ static void set_w_bytes(gtt_plan_s *P, const void *W) {
                 memcpy(dst + 8, &im, 8);
             }
         }
+    append_packed_pairs(P, &P->Wf);
+    append_packed_pairs(P, &P->Wa);
 }
 
 extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
@@ -237,12 +276,52 @@ extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const voi
     const size_t wbytes = (size_t)b * b * P->es;
     (void)wbytes;
     set_w_bytes(P, W);
+    e = cudaMalloc(&P->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->dev_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (P->dev_err) cudaFree(P->dev_err);
+        delete P;
+        return set_error(GTT_ERR_ALLOC, std::string("error flag: ") + cudaGetErrorString(e));
+    }
+    P->sched_tile_bytes = kDefaultTileBytes;
+    P->sched_run_bytes = kDefaultRunBytes;
     gtt_status_t st = make_schedule(P, kDefaultTileBytes, kDefaultRunBytes, &P->passes);
     if (st != GTT_OK) {
+        cudaFree(P->dev_err);
         delete P;
         return st;
     }
     *out = P;
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbuf) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (nbuf < 1 || nbuf > kTmaMaxBuf) return set_error(GTT_ERR_INVALID_ARG, "nbuf must be in [1, 4]");
+    const bool old_use = P->use_tma;
+    const int old_nbuf = P->tma_nbuf;
+    P->use_tma = use_tma != 0;
+    P->tma_nbuf = nbuf;
+    std::vector<PassPlan> passes;
+    gtt_status_t st = make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes);
+    if (st != GTT_OK) {
+        P->use_tma = old_use;
+        P->tma_nbuf = old_nbuf;
+        return st;
+    }
+    P->passes = passes;
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_plan_check(gtt_plan_t P) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "reading the error flag");
+    if (flag) {
+        cudaMemset(P->dev_err, 0, sizeof(int));
+        return set_error(GTT_ERR_TIMEOUT, "a bounded device-side wait expired in a TMA pass");
+    }
     return GTT_OK;
 }
 
@@ -267,6 +346,8 @@ extern "C" gtt_status_t gtt_plan_set_schedule(gtt_plan_t P, long long max_tile_b
     gtt_status_t st = make_schedule(P, max_tile_bytes, min_run_bytes, &passes);
     if (st != GTT_OK) return st;
     P->passes = passes;
+    P->sched_tile_bytes = max_tile_bytes;
+    P->sched_run_bytes = min_run_bytes;
     return GTT_OK;
 }
 
@@ -307,9 +388,13 @@ gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, con
         PassPlan &pp = P->passes[i];
         const void *in = i == 0 ? x : (const void *)y;
         void *outp = y;
-        void *args[4] = {(void *)&in, (void *)&outp, (void *)&pp.params, (void *)Wb.data()};
-        gtt_status_t st = launch_timed(P, pp.kern, dim3(pp.grid), dim3(pp.block), args, pp.smem,
-                                       stream, pp.name);
+        gtt_status_t st;
+        if (pp.tma.on) {
+            st = tma_run(P, pp, Wb, in, outp, stream);
+        } else {
+            void *args[4] = {(void *)&in, (void *)&outp, (void *)&pp.params, (void *)Wb.data()};
+            st = launch_timed(P, pp.kern, dim3(pp.grid), dim3(pp.block), args, pp.smem, stream, pp.name);
+        }
         if (st != GTT_OK) return st;
     }
     return GTT_OK;
@@ -417,14 +502,17 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                     std::to_string(P->passes.size()) + ", \"passes\": [";
     for (size_t i = 0; i < P->passes.size(); ++i) {
         const PassPlan &pp = P->passes[i];
-        char tmp[400];
+        const bool t = pp.tma.on;
+        char tmp[512];
         snprintf(tmp, sizeof tmp,
                  "%s{\"kernel\": \"%s\", \"m0\": %d, \"g\": %d, \"r\": %lld, \"D\": %d, "
                  "\"tile_bytes\": %lld, \"tiles\": %lld, \"grid\": %d, \"block\": %d, \"smem\": %zu, "
-                 "\"ctas_per_sm\": %d, \"vec_mode\": %d}",
-                 i ? ", " : "", pp.name.c_str(), pp.m0, pp.g, pp.r, pp.D,
-                 (long long)pp.params.tile_elems * P->es, pp.params.tiles, pp.grid, pp.block, pp.smem,
-                 pp.ctas_per_sm, pp.params.vec_mode);
+                 "\"ctas_per_sm\": %d, \"vec_mode\": %d, \"tma\": %s, \"nbuf\": %d}",
+                 i ? ", " : "", t ? pp.tma.name.c_str() : pp.name.c_str(), pp.m0, pp.g, pp.r, pp.D,
+                 (long long)pp.params.tile_elems * P->es, pp.params.tiles, t ? pp.tma.grid : pp.grid,
+                 t ? kTmaThreads : pp.block, t ? pp.tma.smem : pp.smem,
+                 t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode, t ? "true" : "false",
+                 t ? pp.tma.params.nbuf : 0);
         s += tmp;
     }
     s += "]}";
@@ -435,6 +523,7 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
 extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
     if (!P) return GTT_OK;
     if (P->dstage) cudaFree(P->dstage);
+    if (P->dev_err) cudaFree(P->dev_err);
     if (P->ws_grad) cudaFree(P->ws_grad);
     if (P->ws_ck) cudaFree(P->ws_ck);
     if (P->ws_dw) cudaFree(P->ws_dw);

@@ -1,6 +1,6 @@
 // Internal interface between the C-ABI layer and the kernel translation units.
 #pragma once
-#include "gtt_pass.cuh"
+#include "gtt_tma.cuh"
 
 namespace gtt {
 
@@ -81,5 +81,26 @@ inline int bwd_rows_host(int b, bool cplx) {
     int R = b;
     while (R * b > budget && R % 2 == 0) R /= 2;
     return R;
+}
+} // namespace gtt
+
+namespace gtt {
+// TMA-pipelined pass kernels (gtt_tma.cuh): b in {2, 4, 8, 16}, D in {1, dmax},
+// contiguous or strided tiles.  nullptr when not instantiated.
+const void *tma_kernel_f64(int b, int d, bool contig);
+const void *tma_kernel_f32(int b, int d, bool contig);
+const void *tma_kernel_c64(int b, int d, bool contig);
+const void *tma_kernel_c128(int b, int d, bool contig);
+const void *tma_kernel_u32(int b, int d, bool contig);
+
+inline const void *tma_kernel(int dtype, int b, int d, bool contig) {
+    switch (dtype) {
+    case 0: return tma_kernel_f64(b, d, contig);
+    case 1: return tma_kernel_f32(b, d, contig);
+    case 2: return tma_kernel_c64(b, d, contig);
+    case 3: return tma_kernel_c128(b, d, contig);
+    case 4: return tma_kernel_u32(b, d, contig);
+    default: return nullptr;
+    }
 }
 } // namespace gtt

@@ -21,6 +21,8 @@
 // window is slid down so it stays inside the g digits; a per-stage mask says
 // which of its digits are applied there.
 #pragma once
+#include <type_traits>
+
 #include "gtt_types.cuh"
 
 namespace gtt {
@@ -60,15 +62,48 @@ __device__ __forceinline__ void apply_digit(T (&v)[cpow(B, D)], const WMat<T, B>
 #pragma unroll
     for (int o = 0; o < cpow(B, D) / B; ++o) {
         const int base = (o / S) * S * B + (o % S);
-        T in[B];
+        if constexpr (std::is_same<T, c64>::value) {
+            // packed FP32x2: the same operations, in the same order, as mul/fma_acc
+            float2 in[B], sw[B];
 #pragma unroll
-        for (int j = 0; j < B; ++j) in[j] = v[base + j * S];
+            for (int j = 0; j < B; ++j) {
+                in[j] = make_float2(v[base + j * S].re, v[base + j * S].im);
+                sw[j] = make_float2(v[base + j * S].im, v[base + j * S].re);
+            }
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            T acc = mul(W.w[i * B], in[0]);
+            for (int i = 0; i < B; ++i) {
+                float2 acc = __ffma2_rn(W.wa[i * B], in[0], make_float2(0.f, 0.f));
+                acc = __ffma2_rn(W.wb[i * B], sw[0], acc);
 #pragma unroll
-            for (int j = 1; j < B; ++j) acc = fma_acc(W.w[i * B + j], in[j], acc);
-            v[base + i * S] = acc;
+                for (int j = 1; j < B; ++j) {
+                    acc = __ffma2_rn(W.wa[i * B + j], in[j], acc);
+                    acc = __ffma2_rn(W.wb[i * B + j], sw[j], acc);
+                }
+                v[base + i * S] = c64{acc.x, acc.y};
+            }
+        } else if constexpr (std::is_same<T, float>::value && B % 2 == 0) {
+            float2 in[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) in[j] = make_float2(v[base + j * S], v[base + j * S]);
+#pragma unroll
+            for (int ip = 0; ip < B / 2; ++ip) {
+                float2 acc = __ffma2_rn(W.wp[ip * B], in[0], make_float2(0.f, 0.f));
+#pragma unroll
+                for (int j = 1; j < B; ++j) acc = __ffma2_rn(W.wp[ip * B + j], in[j], acc);
+                v[base + 2 * ip * S] = acc.x;
+                v[base + (2 * ip + 1) * S] = acc.y;
+            }
+        } else {
+            T in[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) in[j] = v[base + j * S];
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                T acc = mul(W.w[i * B], in[0]);
+#pragma unroll
+                for (int j = 1; j < B; ++j) acc = fma_acc(W.w[i * B + j], in[j], acc);
+                v[base + i * S] = acc;
+            }
         }
     }
 }

@@ -15,6 +15,22 @@ constexpr long long kDefaultRunBytes = 128;
 
 // One pass of a schedule: modes [m0, m0+g) with runs of r elements, register
 // windows of D digits, and its launch geometry.
+// TMA-pipelined variant of a pass (gtt_tma.cuh); present when the tile
+// geometry allows 128-byte TMA rows.  The tensor maps depend on the data
+// pointers and are encoded at launch time (cached per pointer pair).
+struct TmaPass {
+    bool on = false;
+    bool contig = false;
+    TmaParams params;
+    const void *kern = nullptr;
+    int grid = 0, ctas_per_sm = 0;
+    size_t smem = 0;
+    std::string name;
+    // tensor-map cache
+    const void *map_in_ptr = nullptr, *map_out_ptr = nullptr;
+    alignas(64) CUtensorMap map_in, map_out;
+};
+
 struct PassPlan {
     int m0 = 0, g = 0, D = 1;
     long long r = 1;
@@ -23,6 +39,7 @@ struct PassPlan {
     int grid = 0, block = 0, ctas_per_sm = 0;
     size_t smem = 0;
     std::string name;  // kernel name with its template arguments
+    TmaPass tma;
 };
 
 // One pass of the backward schedule: the tile geometry (one stage per digit),
@@ -66,6 +83,10 @@ struct gtt_plan_s {
     bool bwd_ready = false;
     void *ws_grad = nullptr, *ws_ck = nullptr, *ws_dw = nullptr;  // backward workspace
     size_t ws_grad_bytes = 0, ws_ck_bytes = 0, ws_dw_bytes = 0;
+    bool use_tma = true;                 // TMA-pipelined passes where the geometry allows
+    int tma_nbuf = 2;                    // shared-memory buffers per CTA in TMA passes
+    long long sched_tile_bytes = 0, sched_run_bytes = 0;  // limits of the current schedule
+    int *dev_err = nullptr;              // device flag raised by a bounded wait that expired
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
     std::vector<cudaEvent_t> event_pool;
@@ -79,6 +100,10 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block, void **args,
                           size_t smem, cudaStream_t stream, const std::string &name);
 gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget);
+// Attach the TMA variant to a forward pass when its geometry allows (true if attached).
+bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
+gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
+                     void *out, cudaStream_t stream);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
 } // namespace gtt

@@ -1,0 +1,260 @@
+// TMA-pipelined pass of the fast GTT (Sec. 3, Algorithm 1: a group of modes
+// applied in one HBM round trip; same tile geometry as gtt_pass_kernel).
+//
+// Persistent CTAs walk their tiles through a ring of `nbuf` shared-memory
+// buffers.  One thread issues the tensor-memory-accelerator copies:
+// cp.async.bulk.tensor loads (completion counted on an mbarrier per buffer)
+// run nbuf-1 tiles ahead of the compute, and each finished tile leaves by a
+// cp.async.bulk.tensor store, so HBM traffic overlaps the register stages.
+//
+// Shared-memory layout: rows of 128 bytes in the TMA 128B swizzle (16-byte
+// chunk c of row s sits at chunk c ^ (s & 7)); every buffer is 1024-byte
+// aligned.  A tile is either contiguous (the first pass: its M elements are
+// M*es/128 consecutive rows) or strided (M rows of r elements, r*es a
+// multiple of 128: column block cb of 128 bytes occupies rows
+// [cb*M, cb*M + M)).  The swizzle makes both the row-wise accesses of the
+// lowest digits and the column-wise accesses of higher digits conflict-free.
+//
+// Every mbarrier wait is bounded (kSpinLimit polls); on expiry the kernel
+// records the error in p.err, drains its own copies and returns.
+#pragma once
+#include <cuda.h>
+
+#include "gtt_pass.cuh"
+
+namespace gtt {
+
+constexpr int kTmaThreads = 256;
+constexpr int kTmaMaxBuf = 4;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+struct TmaParams {
+    long long tiles;
+    uint32_t M, r, tile_elems, lo_blocks, tile_bytes;
+    uint32_t rows_per_box;    // rows per TMA box (<= 256)
+    uint32_t boxes_per_cb;    // boxes per column block
+    uint32_t cbs;             // column blocks (strided); 1 for contiguous tiles
+    uint32_t units_per_elem;  // tensor-map units per element (2 for 16-byte types)
+    int nbuf;
+    FastDiv div_lo_blocks, div_r;
+    int nstages;
+    int stage_mask[kMaxStages];
+    uint32_t stage_Ba[kMaxStages];  // b^a of the stage's window start a
+    FastDiv stage_divBa[kMaxStages];
+    int *err;  // device flag: 1 = an mbarrier wait expired
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; returns false if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"((uint64_t)map),
+                 "r"(src), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Byte offset of (swizzle row s, byte ccb within the row's 128 bytes).
+__device__ __forceinline__ uint32_t swz(uint32_t s, uint32_t ccb) {
+    return (s << 7) + ((((ccb >> 4) ^ s) & 7u) << 4) + (ccb & 15u);
+}
+
+template <typename T, bool CONTIG> struct TmaTile {
+    static constexpr uint32_t ES = sizeof(T);
+    static constexpr uint32_t R128 = 128 / ES;  // elements per 128-byte row
+    // byte offset of tile element (row, col)
+    __device__ __forceinline__ static uint32_t off(uint32_t row, uint32_t col, uint32_t M) {
+        if constexpr (CONTIG) {
+            return swz(row / R128, (row % R128) * ES);
+        } else {
+            return swz((col / R128) * M + row, (col % R128) * ES);
+        }
+    }
+};
+
+template <typename T, int B, int D, bool CONTIG>
+__global__ void __launch_bounds__(kTmaThreads)
+gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+                    TmaParams p, WMat<T, B> W) {
+    constexpr int RB = cpow(B, D);
+    constexpr int CE = 16 / (int)sizeof(T);
+    using Tile = TmaTile<T, CONTIG>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    unsigned char *sbase = smem_raw + pad;              // generic pointer, 1024-aligned in shared space
+    const uint32_t sbase_s = raw + pad;                  // shared-window address of the same byte
+    const uint32_t bars = sbase_s + (uint32_t)p.nbuf * p.tile_bytes;  // nbuf mbarriers (8 bytes each)
+
+    const uint32_t tid = threadIdx.x, nth = blockDim.x;
+    const long long my_tiles =
+        blockIdx.x < p.tiles ? (p.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (tid == 0) {
+        for (int i = 0; i < p.nbuf; ++i) mbar_init(bars + 8u * i, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // issue the loads of local tile j into buffer j % nbuf (thread 0 only)
+    auto issue_load = [&](long long j) {
+        const long long t = blockIdx.x + j * (long long)gridDim.x;
+        const int buf = (int)(j % p.nbuf);
+        const uint32_t bar = bars + 8u * buf;
+        const uint32_t dst = sbase_s + (uint32_t)buf * p.tile_bytes;
+        mbar_expect_tx(bar, p.tile_bytes);
+        if constexpr (CONTIG) {
+            const long long row0 = t * (long long)(p.tile_bytes >> 7);
+            for (uint32_t k = 0; k < p.boxes_per_cb; ++k)
+                tma_load_2d(dst + k * p.rows_per_box * 128u, &tin, bar, 0, (int)(row0 + (long long)k * p.rows_per_box));
+        } else {
+            const long long hi = t / p.lo_blocks;
+            const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
+            for (uint32_t cb = 0; cb < p.cbs; ++cb)
+                for (uint32_t k = 0; k < p.boxes_per_cb; ++k) {
+                    const int x = (int)((lob * p.r + cb * Tile::R128) * p.units_per_elem);
+                    tma_load_3d(dst + (cb * p.M + k * p.rows_per_box) * 128u, &tin, bar, x,
+                                (int)(k * p.rows_per_box), (int)hi);
+                }
+        }
+    };
+    auto issue_store = [&](long long j) {
+        const long long t = blockIdx.x + j * (long long)gridDim.x;
+        const uint32_t src = sbase_s + (uint32_t)(j % p.nbuf) * p.tile_bytes;
+        if constexpr (CONTIG) {
+            const long long row0 = t * (long long)(p.tile_bytes >> 7);
+            for (uint32_t k = 0; k < p.boxes_per_cb; ++k)
+                tma_store_2d(&tout, src + k * p.rows_per_box * 128u, 0, (int)(row0 + (long long)k * p.rows_per_box));
+        } else {
+            const long long hi = t / p.lo_blocks;
+            const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
+            for (uint32_t cb = 0; cb < p.cbs; ++cb)
+                for (uint32_t k = 0; k < p.boxes_per_cb; ++k) {
+                    const int x = (int)((lob * p.r + cb * Tile::R128) * p.units_per_elem);
+                    tma_store_3d(&tout, src + (cb * p.M + k * p.rows_per_box) * 128u, x,
+                                 (int)(k * p.rows_per_box), (int)hi);
+                }
+        }
+        bulk_commit();
+    };
+
+    const int ahead = p.nbuf > 1 ? p.nbuf - 1 : 1;
+    if (tid == 0)
+        for (long long j = 0; j < ahead && j < my_tiles; ++j) issue_load(j);
+
+    bool failed = false;
+    long long consumed = 0;  // local tiles whose load has been waited for
+    for (long long i = 0; i < my_tiles; ++i) {
+        const int buf = (int)(i % p.nbuf);
+        if (tid == 0) {
+            // refill the buffer freed by tile i-1 with tile i+nbuf-1 (tile i itself when nbuf == 1)
+            const long long j = p.nbuf > 1 ? i + p.nbuf - 1 : i;
+            if (j < my_tiles && (p.nbuf > 1 || i > 0)) {
+                if (i > 0) bulk_wait_read_all();
+                issue_load(j);
+            }
+        }
+        const bool ok = mbar_wait(bars + 8u * buf, (uint32_t)((i / p.nbuf) & 1));
+        if (__syncthreads_or(!ok)) {  // CTA-uniform decision
+            failed = true;
+            break;
+        }
+        consumed = i + 1;
+        unsigned char *tb = sbase + (size_t)buf * p.tile_bytes;
+
+        const uint32_t nslots = p.tile_elems / RB;
+        for (int st = 0; st < p.nstages; ++st) {
+            const uint32_t Ba = p.stage_Ba[st];
+            const int mask = p.stage_mask[st];
+            for (uint32_t slot = tid; slot < nslots; slot += nth) {
+                const uint32_t rest = p.div_r.div(slot);
+                const uint32_t col = slot - rest * p.r;
+                const uint32_t high = p.stage_divBa[st].div(rest);
+                const uint32_t low = rest - high * Ba;
+                const uint32_t row0 = low + high * Ba * RB;
+                T v[RB];
+                if constexpr (CONTIG && (RB % CE == 0)) {
+                    if (Ba == 1) {  // the window holds the lowest digits: 16-byte chunks
+#pragma unroll
+                        for (int q = 0; q < RB; q += CE)
+                            *reinterpret_cast<int4 *>(&v[q]) =
+                                *reinterpret_cast<const int4 *>(tb + Tile::off(row0 + q, 0, p.M));
+                        apply_window<T, B, D>(v, mask, W);
+#pragma unroll
+                        for (int q = 0; q < RB; q += CE)
+                            *reinterpret_cast<int4 *>(tb + Tile::off(row0 + q, 0, p.M)) =
+                                *reinterpret_cast<const int4 *>(&v[q]);
+                        continue;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    v[q] = *reinterpret_cast<const T *>(tb + Tile::off(row0 + q * Ba, col, p.M));
+                apply_window<T, B, D>(v, mask, W);
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    *reinterpret_cast<T *>(tb + Tile::off(row0 + q * Ba, col, p.M)) = v[q];
+            }
+            __syncthreads();
+        }
+        fence_proxy_async();  // make this thread's smem writes visible to the TMA engine
+        __syncthreads();
+        if (tid == 0) issue_store(i);
+    }
+
+    if (failed) {
+        if (tid == 0) {
+            atomicExch(p.err, 1);
+            // drain the loads still in flight for this CTA (bounded), then its stores
+            for (long long j = consumed; j < my_tiles && j < consumed + p.nbuf; ++j)
+                mbar_wait(bars + 8u * (uint32_t)(j % p.nbuf), (uint32_t)((j / p.nbuf) & 1));
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+    __syncthreads();
+}
+
+} // namespace gtt

@@ -92,6 +92,20 @@ __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * c
 template <typename T, int B> struct WMat {
     T w[B * B];
 };
+// complex64 adds, for the packed FP32x2 FMAs of apply_digit, the pairs
+// wa = (re, re) and wb = (-im, im) of every entry: one complex MAC is then
+// acc += wa * (v.re, v.im) followed by acc += wb * (v.im, v.re).
+template <int B> struct WMat<c64, B> {
+    c64 w[B * B];
+    float2 wa[B * B];
+    float2 wb[B * B];
+};
+// FP32 with even B adds the row pairs wp[(i/2)*B + j] = (W[i][j], W[i+1][j]),
+// so two outputs of a fibre advance with one packed FMA.
+template <int B> struct WMat<float, B> {
+    float w[B * B];
+    float2 wp[(B % 2 == 0) ? B * B / 2 : 1];
+};
 
 // Unsigned 32-bit division by a runtime divisor d >= 1 via a precomputed
 // multiplier (the round-up method of Granlund and Montgomery, "Division by

@@ -249,3 +249,41 @@ def test_misaligned_and_null_pointers_rejected(g):
     st = lib.gtt_forward(plan._h, None, buf.data_ptr(), None)
     assert st == 1
     assert b"aligned" in lib.gtt_last_error() or lib.gtt_last_error()
+
+
+# ------------------------------------------------- TMA-pipelined passes
+
+@pytest.mark.parametrize("nbuf", [1, 2, 3, 4])
+@pytest.mark.parametrize("b,n,dt,sched", [(4, 10, "c64", (32768, 128)), (2, 18, "f32", (16384, 128)),
+                                          (8, 6, "f64", (32768, 128)), (16, 4, "f32", (16384, 1024)),
+                                          (4, 9, "c128", (65536, 128)), (2, 16, "f32", (131072, 256)),
+                                          (16, 5, "c64", (65536, 2048))])
+def test_tma_pipeline_matches_oracle(g, nbuf, b, n, dt, sched):
+    """TMA-staged passes (1..4 buffers) give the oracle's result; the plan's
+    bounded-wait flag stays clear."""
+    rng = np.random.default_rng(7000 + b + nbuf)
+    W, x = make_inputs(b, n, 3, dt, rng)
+    plan = g.Plan(W, n, dt, 3)
+    plan.set_schedule(*sched)
+    plan.set_pipeline(True, nbuf)
+    d = plan.describe()
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    y = plan.forward(xd)
+    xr = plan.inverse(y)
+    torch.cuda.synchronize()
+    plan.check()
+    ref = oracle.modes(up(W), up(x))
+    assert rel_l2(y.cpu().numpy(), ref) <= TOL[dt], d
+    assert rel_l2(xr.cpu().numpy(), up(x)) <= 2 * TOL[dt]
+    # the same schedule without TMA gives bitwise identical results
+    plan.set_pipeline(False, nbuf)
+    y2 = plan.forward(xd)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(y.cpu().numpy(), y2.cpu().numpy())
+
+
+def test_tma_used_for_power_of_two_bases(g):
+    rng = np.random.default_rng(7100)
+    W, x = make_inputs(4, 13, 1, "c64", rng)
+    plan = g.Plan(W, 13, "c64", 1)
+    assert all(p["tma"] for p in plan.describe()["passes"])
