@@ -70,28 +70,37 @@ __device__ __forceinline__ void apply_digit(T (&v)[cpow(B, D)], const WMat<T, B>
                 in[j] = make_float2(v[base + j * S].re, v[base + j * S].im);
                 sw[j] = make_float2(v[base + j * S].im, v[base + j * S].re);
             }
+            // inputs outermost: the B accumulators advance together (independent
+            // chains between dependent FMAs); each output still sums j = 0..B-1 in order
+            float2 acc[B];
 #pragma unroll
-            for (int i = 0; i < B; ++i) {
-                float2 acc = __ffma2_rn(W.wa[i * B], in[0], make_float2(0.f, 0.f));
-                acc = __ffma2_rn(W.wb[i * B], sw[0], acc);
+            for (int i = 0; i < B; ++i) acc[i] = __ffma2_rn(W.wa[i * B], in[0], make_float2(0.f, 0.f));
 #pragma unroll
-                for (int j = 1; j < B; ++j) {
-                    acc = __ffma2_rn(W.wa[i * B + j], in[j], acc);
-                    acc = __ffma2_rn(W.wb[i * B + j], sw[j], acc);
-                }
-                v[base + i * S] = c64{acc.x, acc.y};
+            for (int i = 0; i < B; ++i) acc[i] = __ffma2_rn(W.wb[i * B], sw[0], acc[i]);
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+#pragma unroll
+                for (int i = 0; i < B; ++i) acc[i] = __ffma2_rn(W.wa[i * B + j], in[j], acc[i]);
+#pragma unroll
+                for (int i = 0; i < B; ++i) acc[i] = __ffma2_rn(W.wb[i * B + j], sw[j], acc[i]);
             }
+#pragma unroll
+            for (int i = 0; i < B; ++i) v[base + i * S] = c64{acc[i].x, acc[i].y};
         } else if constexpr (std::is_same<T, float>::value && B % 2 == 0) {
             float2 in[B];
 #pragma unroll
             for (int j = 0; j < B; ++j) in[j] = make_float2(v[base + j * S], v[base + j * S]);
+            float2 acc[B / 2];
+#pragma unroll
+            for (int ip = 0; ip < B / 2; ++ip) acc[ip] = __ffma2_rn(W.wp[ip * B], in[0], make_float2(0.f, 0.f));
+#pragma unroll
+            for (int j = 1; j < B; ++j)
+#pragma unroll
+                for (int ip = 0; ip < B / 2; ++ip) acc[ip] = __ffma2_rn(W.wp[ip * B + j], in[j], acc[ip]);
 #pragma unroll
             for (int ip = 0; ip < B / 2; ++ip) {
-                float2 acc = __ffma2_rn(W.wp[ip * B], in[0], make_float2(0.f, 0.f));
-#pragma unroll
-                for (int j = 1; j < B; ++j) acc = __ffma2_rn(W.wp[ip * B + j], in[j], acc);
-                v[base + 2 * ip * S] = acc.x;
-                v[base + (2 * ip + 1) * S] = acc.y;
+                v[base + 2 * ip * S] = acc[ip].x;
+                v[base + (2 * ip + 1) * S] = acc[ip].y;
             }
         } else {
             T in[B];

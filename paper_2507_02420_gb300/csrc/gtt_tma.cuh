@@ -28,6 +28,13 @@ constexpr int kTmaThreads = 256;
 constexpr int kTmaMaxBuf = 4;
 constexpr uint32_t kSpinLimit = 1u << 24;
 
+// CTAs per SM the register allocation is sized for: three when the register
+// window is small (<= 16 elements, <= 128 bytes of data per thread, b <= 8),
+// else one.
+__host__ __device__ constexpr int tma_min_blocks(int es, int B, int D) {
+    return (B <= 8 && cpow(B, D) <= 16 && cpow(B, D) * es <= 128) ? 3 : 1;
+}
+
 struct TmaParams {
     long long tiles;
     uint32_t M, r, tile_elems, lo_blocks, tile_bytes;
@@ -116,7 +123,7 @@ template <typename T, bool CONTIG> struct TmaTile {
 };
 
 template <typename T, int B, int D, bool CONTIG>
-__global__ void __launch_bounds__(kTmaThreads)
+__global__ void __launch_bounds__(kTmaThreads, tma_min_blocks((int)sizeof(T), B, D))
 gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                     TmaParams p, WMat<T, B> W) {
     constexpr int RB = cpow(B, D);

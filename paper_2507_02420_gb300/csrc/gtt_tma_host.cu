@@ -79,6 +79,7 @@ bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf) {
     const size_t smem = (size_t)nbuf * tile_bytes + 1024 + 8 * kTmaMaxBuf;
     if (smem > (size_t)P->smem_optin) return false;
     if (allow_max_smem(k, P->smem_optin) != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) return false;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTmaThreads, smem) != cudaSuccess || per_sm < 1)
         return false;
