@@ -349,6 +349,8 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof,
         "e2e": e2e,
     }
+    if not args.no_extras and world == 1:
+        line["extras"] = run_extras(g, dev, peaks)
     if not args.no_cpu_baseline and world == 1:
         v, cores, reps, el = oracle_pairs_gelems(W, x, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
@@ -356,6 +358,79 @@ def run_gpu(args, rank, world, local_rank):
                                           f"vector, complex128 mode loop, {el:.1f} s"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_device(fn, reps: int, warm: int = 3) -> float:
+    """Mean device seconds of fn() over reps calls (CUDA events, current stream)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / 1e3 / reps
+
+
+def run_extras(g, dev, peaks):
+    """The other hot-path rows, each timed on its own workload (not part of
+    `value`): the b=16 FP32 contraction path, the b=8 training step (forward +
+    hand-written backward) and the 1000-request grouped launch."""
+    import torch
+    out = {}
+    hbm = float(peaks["hbm_gbs"])
+    # b = 16, n = 6, batch 64, FP32: CUDA-core contraction path
+    W2, x2 = gi.config_inputs(2)
+    p2 = g.Plan(W2, 6, "f32", 64)
+    x2d = torch.from_numpy(x2).to(dev)
+    del x2
+    y2d = torch.empty_like(x2d)
+    t = _time_device(lambda: p2.forward(x2d, out=y2d), reps=10)
+    n2 = x2d.numel()
+    out["b16_n6_batch64_f32"] = {
+        "path": "fp32_cuda_core", "ms": t * 1e3, "gelem_s": n2 / t / 1e9,
+        "passes": len(p2.describe()["passes"]),
+        "hbm_gbs_algorithmic": len(p2.describe()["passes"]) * 2 * n2 * 4 / t / 1e9,
+        "hbm_frac": len(p2.describe()["passes"]) * 2 * n2 * 4 / t / 1e9 / hbm}
+    del x2d, y2d, p2
+    torch.cuda.empty_cache()
+    # b = 8, n = 7, batch 32, FP32 training step: forward + backward (dx, dW)
+    W3, x3 = gi.config_inputs(3)
+    p3 = g.Plan(W3, 7, "f32", 32)
+    x3d = torch.from_numpy(x3).to(dev)
+    y3d = torch.empty_like(x3d)
+    dy3 = torch.from_numpy(gi.config3_mask()).to(dev) * 2.0
+
+    def train_step():
+        p3.forward(x3d, out=y3d)
+        p3.backward(x3d, dy3)
+    t = _time_device(train_step, reps=10)
+    out["b8_n7_batch32_train_step"] = {"ms": t * 1e3, "gelem_s": x3d.numel() / t / 1e9,
+                                       "includes": "gtt_forward + gtt_backward (dx and dW)"}
+    del x3d, y3d, dy3, p3
+    torch.cuda.empty_cache()
+    # 1000 uneven requests in one persistent launch (CUDA graph)
+    reqs = []
+    elems = 0
+    nbytes = 0
+    for r in gi.grouped_requests():
+        W, x = gi.request_inputs(r)
+        xd = torch.from_numpy(x).to(dev)
+        reqs.append(dict(b=r.b, n=r.n, dtype=r.dtype, W=W, x=xd, y=torch.empty_like(xd)))
+        elems += x.size
+        nbytes += x.nbytes
+    grp = g.Group(reqs)
+    t = _time_device(grp.execute, reps=10)
+    grp.check()
+    d = grp.describe()
+    out["grouped_1000_uneven"] = {
+        "ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
+        "kernel_launches_per_execute": 1, "work_items": d["work_items"],
+        "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9}
+    return out
 
 
 def main():
@@ -366,6 +441,8 @@ def main():
     ap.add_argument("--impl", choices=["gtt", "reference"], default="gtt")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-row measurements of the other workloads")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()

@@ -113,6 +113,34 @@ gtt_status_t gtt_plan_set_schedule(gtt_plan_t plan, long long max_tile_bytes,
                                    long long min_run_bytes);
 
 /*
+ * gtt_plan_set_passes -- set the fusion schedule explicitly.  Pass k applies
+ * digits[k] consecutive modes (the first pass starts at digit 0, each next
+ * pass where the previous one ended; the digits must sum to n) to tiles of
+ * b^digits[k] rows of runs[k] contiguous elements.  runs[0] must be 1; for
+ * k > 0, runs[k] must divide b^(digits before pass k).  A tile (rows x run)
+ * must fit 220 KiB.  Errors: GTT_ERR_INVALID_ARG (bad counts, sums, runs or
+ * sizes), GTT_ERR_UNSUPPORTED, GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_plan_set_passes(gtt_plan_t plan, int count, const int *digits, const long long *runs);
+
+/*
+ * gtt_plan_autotune -- time up to max_candidates (<= 0: 64) candidate
+ * schedules (mode groups of at most four passes, run lengths, TMA pipeline
+ * depth) on scratch buffers of the plan's size, keep the fastest in the plan
+ * and record it in the process-wide autotune cache, keyed by GPU name, b, n,
+ * dtype and batch.  Allocates and frees two data-sized device buffers;
+ * synchronizes the device.  gtt_plan_create applies a cached schedule when
+ * one exists; the environment variable GTT_AUTOTUNE_CACHE names a cache file
+ * loaded at the first plan creation, and GTT_AUTOTUNE=on tunes uncached
+ * shapes at creation.
+ * gtt_autotune_cache_load / _save -- merge a cache file into the process
+ * cache / write the process cache (one JSON object per line).
+ */
+gtt_status_t gtt_plan_autotune(gtt_plan_t plan, int max_candidates);
+gtt_status_t gtt_autotune_cache_load(const char *path);
+gtt_status_t gtt_autotune_cache_save(const char *path);
+
+/*
  * gtt_plan_set_pipeline -- choose how the forward/inverse passes stage their
  * tiles: use_tma != 0 streams tiles through `nbuf` (1..4) shared-memory
  * buffers with tensor-memory-accelerator copies where the tile geometry allows
@@ -214,6 +242,41 @@ gtt_status_t gtt_plan_describe(gtt_plan_t plan, char *buf, size_t len);
  */
 gtt_status_t gtt_plan_set_timing(gtt_plan_t plan, int enable);
 gtt_status_t gtt_plan_timing(gtt_plan_t plan, char *buf, size_t len);
+
+/* ----------------------------------------------------------------------
+ * Grouped transforms: many independent transforms of uneven b, n and dtype
+ * (each y = W^{(x)n} x of Def. 2.3 with its own W) executed by ONE
+ * persistent kernel launch, captured once in a CUDA graph.
+ * -------------------------------------------------------------------- */
+typedef struct {
+    int b;              /* 2..8 or 16                                         */
+    int n;              /* >= 1                                               */
+    gtt_dtype_t dtype;  /* GTT_F32 or GTT_C64                                 */
+    const void *W;      /* HOST, b*b elements row-major (copied at creation)  */
+    const void *x;      /* device, N = b^n elements, 16-byte aligned          */
+    void *y;            /* device, N elements, 16-byte aligned (may equal x)  */
+    int inverse;        /* 0: y = G_N x;  1: y = G_N^dagger x (W^H)           */
+} gtt_request_t;
+
+/*
+ * gtt_group_create -- plan `count` requests for one persistent launch.  Each
+ * distinct (b, n, dtype) gets its mode-group schedule from the autotune cache
+ * (gtt_plan_autotune / GTT_AUTOTUNE_CACHE) or the fixed rule.  Work items are
+ * (request, pass, tile); a pass of a request starts after the request's
+ * previous pass (a bounded device-side wait; expiry raises GTT_ERR_TIMEOUT in
+ * gtt_group_check).  The pointers in the requests are fixed for the group's
+ * lifetime.  Errors: GTT_ERR_INVALID_ARG, GTT_ERR_UNSUPPORTED (b or dtype
+ * outside the supported set), GTT_ERR_ALLOC, GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_request_t *reqs);
+/* Run every request of the group: one graph launch (a counter reset and one
+ * kernel) on `stream`; the graph is captured on the first call. */
+gtt_status_t gtt_group_execute(gtt_group_t group, gtt_stream_t stream);
+/* Wait for the device; GTT_ERR_TIMEOUT if a bounded wait expired (then cleared). */
+gtt_status_t gtt_group_check(gtt_group_t group);
+/* One-line JSON: requests, elements, work items, segments, grid, shared memory. */
+gtt_status_t gtt_group_describe(gtt_group_t group, char *buf, size_t len);
+gtt_status_t gtt_group_destroy(gtt_group_t group);
 
 /* Release the plan and everything it owns.  NULL is accepted. */
 gtt_status_t gtt_plan_destroy(gtt_plan_t plan);

@@ -24,6 +24,10 @@ SIGNATURES = {
     "gtt_plan_set_w": (_I, [_P, _P]),
     "gtt_plan_set_schedule": (_I, [_P, _LL, _LL]),
     "gtt_plan_set_pipeline": (_I, [_P, _I, _I]),
+    "gtt_plan_set_passes": (_I, [_P, _I, _P, _P]),
+    "gtt_plan_autotune": (_I, [_P, _I]),
+    "gtt_autotune_cache_load": (_I, [ctypes.c_char_p]),
+    "gtt_autotune_cache_save": (_I, [ctypes.c_char_p]),
     "gtt_plan_check": (_I, [_P]),
     "gtt_forward": (_I, [_P, _P, _P, _P]),
     "gtt_inverse": (_I, [_P, _P, _P, _P]),
@@ -36,6 +40,11 @@ SIGNATURES = {
     "gtt_plan_timing": (_I, [_P, ctypes.c_char_p, _S]),
     "gtt_plan_destroy": (_I, [_P]),
     "gtt_last_error": (ctypes.c_char_p, []),
+    "gtt_group_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "gtt_group_execute": (_I, [_P, _P]),
+    "gtt_group_check": (_I, [_P]),
+    "gtt_group_describe": (_I, [_P, ctypes.c_char_p, _S]),
+    "gtt_group_destroy": (_I, [_P]),
 }
 
 _lock = threading.Lock()

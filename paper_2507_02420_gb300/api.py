@@ -98,6 +98,19 @@ class Plan:
         check(self._lib.gtt_plan_set_schedule(self._h, int(max_tile_bytes), int(min_run_bytes)),
               "gtt_plan_set_schedule")
 
+    def set_passes(self, digits, runs):
+        """Explicit schedule: pass k applies digits[k] modes on rows of runs[k] elements."""
+        d = np.ascontiguousarray(digits, dtype=np.int32)
+        r = np.ascontiguousarray(runs, dtype=np.int64)
+        if d.shape != r.shape:
+            raise ValueError("digits and runs must have the same length")
+        check(self._lib.gtt_plan_set_passes(self._h, len(d), d.ctypes.data, r.ctypes.data),
+              "gtt_plan_set_passes")
+
+    def autotune(self, max_candidates: int = 64):
+        """Time candidate schedules and keep the fastest (recorded in the cache)."""
+        check(self._lib.gtt_plan_autotune(self._h, int(max_candidates)), "gtt_plan_autotune")
+
     def set_pipeline(self, use_tma: bool = True, nbuf: int = 2):
         check(self._lib.gtt_plan_set_pipeline(self._h, int(bool(use_tma)), int(nbuf)),
               "gtt_plan_set_pipeline")
@@ -180,3 +193,11 @@ class Plan:
         check(self._lib.gtt_inverse_host(self._h, ya.ctypes.data, xa.ctypes.data, _stream_ptr(stream)),
               "gtt_inverse_host")
         return x
+
+
+def autotune_cache_load(path: str):
+    check(load().gtt_autotune_cache_load(path.encode()), "gtt_autotune_cache_load")
+
+
+def autotune_cache_save(path: str):
+    check(load().gtt_autotune_cache_save(path.encode()), "gtt_autotune_cache_save")

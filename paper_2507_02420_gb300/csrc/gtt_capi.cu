@@ -291,7 +291,54 @@ extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const voi
         delete P;
         return st;
     }
+    // a schedule from the autotune cache replaces the fixed rule; with
+    // GTT_AUTOTUNE=on an uncached shape is tuned now
+    if (!tune_apply_cached(P)) {
+        const char *at = std::getenv("GTT_AUTOTUNE");
+        if (at && std::strcmp(at, "on") == 0) autotune(P, 64);
+    }
     *out = P;
+    return GTT_OK;
+}
+
+namespace gtt {
+// Build an explicit schedule: pass k covers digits[k] modes with runs[k].
+gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits, const long long *runs,
+                                    std::vector<PassPlan> *out) {
+    if (count < 1 || count > 64 || !digits || !runs) return set_error(GTT_ERR_INVALID_ARG, "bad pass list");
+    const int b = P->b, es = P->es, DM = dmax_bytes(es, b);
+    int m0 = 0;
+    std::vector<PassPlan> passes;
+    for (int k = 0; k < count; ++k) {
+        const int g = digits[k];
+        const long long r = runs[k];
+        if (g < 1 || m0 + g > P->n) return set_error(GTT_ERR_INVALID_ARG, "pass digits out of range");
+        long long L = 1, M = 1;
+        for (int i = 0; i < m0; ++i) L *= b;
+        for (int i = 0; i < g; ++i) M *= b;
+        if (r < 1 || L % r != 0 || (k == 0 && r != 1)) return set_error(GTT_ERR_INVALID_ARG, "run must divide b^m0");
+        if (M * r * es > 220 * 1024) return set_error(GTT_ERR_INVALID_ARG, "tile above 220 KiB");
+        PassPlan pp;
+        gtt_status_t st = build_pass(P, m0, g, r, g >= DM ? DM : 1, &pp);
+        if (st != GTT_OK) return st;
+        if (P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
+        passes.push_back(pp);
+        m0 += g;
+    }
+    if (m0 != P->n) return set_error(GTT_ERR_INVALID_ARG, "pass digits must sum to n");
+    *out = passes;
+    return GTT_OK;
+}
+} // namespace gtt
+
+extern "C" gtt_status_t gtt_plan_set_passes(gtt_plan_t P, int count, const int *digits, const long long *runs) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    std::vector<PassPlan> passes;
+    gtt_status_t st = make_explicit_schedule(P, count, digits, runs, &passes);
+    if (st != GTT_OK) return st;
+    P->passes = passes;
+    P->explicit_g.assign(digits, digits + count);
+    P->explicit_r.assign(runs, runs + count);
     return GTT_OK;
 }
 
@@ -303,7 +350,10 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     P->use_tma = use_tma != 0;
     P->tma_nbuf = nbuf;
     std::vector<PassPlan> passes;
-    gtt_status_t st = make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes);
+    gtt_status_t st = P->explicit_g.empty()
+                          ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
+                          : make_explicit_schedule(P, (int)P->explicit_g.size(), P->explicit_g.data(),
+                                                   P->explicit_r.data(), &passes);
     if (st != GTT_OK) {
         P->use_tma = old_use;
         P->tma_nbuf = old_nbuf;
@@ -346,6 +396,8 @@ extern "C" gtt_status_t gtt_plan_set_schedule(gtt_plan_t P, long long max_tile_b
     gtt_status_t st = make_schedule(P, max_tile_bytes, min_run_bytes, &passes);
     if (st != GTT_OK) return st;
     P->passes = passes;
+    P->explicit_g.clear();
+    P->explicit_r.clear();
     P->sched_tile_bytes = max_tile_bytes;
     P->sched_run_bytes = min_run_bytes;
     return GTT_OK;

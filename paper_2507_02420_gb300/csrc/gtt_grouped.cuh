@@ -1,0 +1,198 @@
+// Grouped persistent launch: many transforms of uneven b, n and dtype in one
+// kernel (each transform is the fast GTT of Sec. 3 with its own W).
+//
+// The work list is a sequence of segments; a segment is one pass of one
+// request, split into tiles (the tile geometry of gtt_pass_kernel).  CTAs take
+// work items (segment, tile) from a global atomic counter in list order.  A
+// segment of pass p > 0 may only start once every tile of pass p-1 of the same
+// request is done; the host orders the list so that pass p of request q comes
+// `lag` requests after pass p-1 of q, so the wait is normally already
+// satisfied and the previous pass's output is still in L2.  Because items are
+// taken in order and a CTA finishes its item before taking the next, every
+// awaited item has been taken by a running CTA, so the waits always end; each
+// is still bounded (kGroupSpinLimit polls) and an expiry raises the error flag.
+//
+// W of every request lives in a device blob (the kernels' parameter layout);
+// each item copies its W into shared memory.  Tile data is read with
+// L2-coherent loads (ld.global.cg): an earlier pass on another SM wrote it.
+#pragma once
+#include "gtt_internal.h"
+
+namespace gtt {
+
+constexpr int kGroupMaxPass = 6;
+constexpr int kGroupThreads = 256;
+constexpr uint32_t kGroupSpinLimit = 1u << 26;
+
+struct GroupPass {
+    PassParams p;
+    int D;
+};
+
+struct GroupReq {
+    const void *x;
+    void *y;
+    int b, dtype, npass, w_off;
+    GroupPass pass[kGroupMaxPass];
+};
+
+struct GroupSeg {
+    int req, pass, dep;  // dep: segment that must complete first, -1 if none
+    int pad_;
+    long long first_item, tiles;
+};
+
+struct GroupArgs {
+    const GroupReq *reqs;
+    const GroupSeg *segs;
+    int nsegs;
+    long long total_items;
+    const unsigned char *wblob;
+    unsigned long long *work_counter;  // zeroed before every launch
+    unsigned int *done;                // tiles completed per segment, zeroed before every launch
+    int *err;
+    int w_smem_bytes;                  // bytes reserved for W at the start of shared memory
+};
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T *p) {
+    if constexpr (sizeof(T) == 4) {
+        unsigned v = __ldcg(reinterpret_cast<const unsigned *>(p));
+        return *reinterpret_cast<T *>(&v);
+    } else {
+        unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long *>(p));
+        return *reinterpret_cast<T *>(&v);
+    }
+}
+
+// One tile of one pass (shared-memory staging as in gtt_pass_kernel).
+template <typename T, int B, int D>
+__device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p, long long t, T *s,
+                                        const WMat<T, B> &W) {
+    constexpr int RB = cpow(B, D);
+    const uint32_t tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t tile_elems = p.tile_elems, r = p.r;
+    const long long hi = t / p.lo_blocks;
+    const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
+    const long long base = hi * p.L * (long long)p.M + (long long)lob * r;
+    for (uint32_t e = tid; e < tile_elems; e += nth) {
+        const uint32_t row = p.div_r.div(e), col = e - row * r;
+        s[spos<RB>(e)] = ld_cg(in + base + (long long)row * p.L + col);
+    }
+    __syncthreads();
+    const uint32_t nslots = tile_elems / RB;
+    for (int st = 0; st < p.nstages; ++st) {
+        const uint32_t strideA = p.stage_strideA[st];
+        const int mask = p.stage_mask[st];
+        for (uint32_t slot = tid; slot < nslots; slot += nth) {
+            const uint32_t rest = p.div_r.div(slot);
+            const uint32_t col = slot - rest * r;
+            const uint32_t high = p.stage_divBa[st].div(rest);
+            const uint32_t low = rest - high * p.stage_divBa[st].d;
+            const uint32_t e0 = high * (strideA * RB) + low * r + col;
+            T v[RB];
+#pragma unroll
+            for (int q = 0; q < RB; ++q) v[q] = s[spos<RB>(e0 + q * strideA)];
+            apply_window<T, B, D>(v, mask, W);
+#pragma unroll
+            for (int q = 0; q < RB; ++q) s[spos<RB>(e0 + q * strideA)] = v[q];
+        }
+        __syncthreads();
+    }
+    for (uint32_t e = tid; e < tile_elems; e += nth) {
+        const uint32_t row = p.div_r.div(e), col = e - row * r;
+        out[base + (long long)row * p.L + col] = s[spos<RB>(e)];
+    }
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void group_dispatch_d(const GroupReq &rq, const GroupPass &gp, long long t,
+                                                 unsigned char *smem, int w_smem_bytes, bool first) {
+    constexpr int DM = dmax_bytes((int)sizeof(T), B);
+    const T *in = reinterpret_cast<const T *>(first ? rq.x : (const void *)rq.y);
+    T *out = reinterpret_cast<T *>(rq.y);
+    const WMat<T, B> &W = *reinterpret_cast<const WMat<T, B> *>(smem);
+    T *s = reinterpret_cast<T *>(smem + w_smem_bytes);
+    if (gp.D == DM)
+        group_tile<T, B, DM>(in, out, gp.p, t, s, W);
+    else
+        group_tile<T, B, 1>(in, out, gp.p, t, s, W);
+}
+
+template <typename T>
+__device__ __forceinline__ void group_dispatch(const GroupReq &rq, const GroupPass &gp, long long t,
+                                               unsigned char *smem, int w_smem_bytes, bool first) {
+    switch (rq.b) {
+    case 2: group_dispatch_d<T, 2>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 3: group_dispatch_d<T, 3>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 4: group_dispatch_d<T, 4>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 5: group_dispatch_d<T, 5>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 6: group_dispatch_d<T, 6>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 7: group_dispatch_d<T, 7>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 8: group_dispatch_d<T, 8>(rq, gp, t, smem, w_smem_bytes, first); break;
+    case 16: group_dispatch_d<T, 16>(rq, gp, t, smem, w_smem_bytes, first); break;
+    default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kGroupThreads) gtt_grouped_kernel(GroupArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_seg;
+    const uint32_t tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const long long item = (long long)atomicAdd(a.work_counter, 1ull);
+            int lo = 0, hi = a.nsegs - 1, seg = 0;
+            if (item < a.total_items) {  // last segment whose first_item <= item
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.segs[mid].first_item <= item) {
+                        seg = mid;
+                        lo = mid + 1;
+                    } else {
+                        hi = mid - 1;
+                    }
+                }
+                const int dep = a.segs[seg].dep;
+                if (dep >= 0) {  // bounded wait for the previous pass of this request
+                    const unsigned int need = (unsigned int)a.segs[dep].tiles;
+                    uint32_t spins = 0;
+                    while (*((volatile unsigned int *)&a.done[dep]) < need) {
+                        if (++spins > kGroupSpinLimit) {
+                            atomicExch(a.err, 1);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    __threadfence();
+                }
+            }
+            s_item = item;
+            s_seg = seg;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= a.total_items) break;
+        const GroupSeg &sg = a.segs[s_seg];
+        const GroupReq &rq = a.reqs[sg.req];
+        const GroupPass &gp = rq.pass[sg.pass];
+        // W of this request into shared memory
+        {
+            const int wb = a.w_smem_bytes;
+            const int4 *src = reinterpret_cast<const int4 *>(a.wblob + rq.w_off);
+            int4 *dst = reinterpret_cast<int4 *>(smem);
+            for (int i = tid; i < wb / 16; i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const long long t = item - sg.first_item;
+        if (rq.dtype == 1)
+            group_dispatch<float>(rq, gp, t, smem, a.w_smem_bytes, sg.pass == 0);
+        else
+            group_dispatch<c64>(rq, gp, t, smem, a.w_smem_bytes, sg.pass == 0);
+        __threadfence();  // this thread's stores before the completion count
+        __syncthreads();
+        if (tid == 0) atomicAdd(&a.done[s_seg], 1u);
+    }
+}
+
+} // namespace gtt

@@ -28,7 +28,7 @@ struct TmaPass {
     std::string name;
     // tensor-map cache
     const void *map_in_ptr = nullptr, *map_out_ptr = nullptr;
-    alignas(64) CUtensorMap map_in, map_out;
+    CUtensorMap map_in, map_out;  // the type carries its own 64-byte alignment
 };
 
 struct PassPlan {
@@ -62,7 +62,11 @@ struct TimingRecord {
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
 // (one limit per kernel, so passes of different tile sizes can share it).
 inline cudaError_t allow_max_smem(const void *kern, int optin) {
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
 }
 
 gtt_status_t set_error(gtt_status_t st, const std::string &msg);
@@ -86,6 +90,8 @@ struct gtt_plan_s {
     bool use_tma = true;                 // TMA-pipelined passes where the geometry allows
     int tma_nbuf = 2;                    // shared-memory buffers per CTA in TMA passes
     long long sched_tile_bytes = 0, sched_run_bytes = 0;  // limits of the current schedule
+    std::vector<int> explicit_g;         // explicit schedule (gtt_plan_set_passes), else empty
+    std::vector<long long> explicit_r;
     int *dev_err = nullptr;              // device flag raised by a bounded wait that expired
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
@@ -100,6 +106,12 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block, void **args,
                           size_t smem, cudaStream_t stream, const std::string &name);
 gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget);
+// Autotuner (gtt_autotune.cu): apply a cached schedule to a plan (true if
+// one existed), or time candidates and keep the fastest.
+bool tune_apply_cached(gtt_plan_s *P);
+gtt_status_t autotune(gtt_plan_s *P, int max_candidates);
+gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits, const long long *runs,
+                                    std::vector<PassPlan> *out);
 // Attach the TMA variant to a forward pass when its geometry allows (true if attached).
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
