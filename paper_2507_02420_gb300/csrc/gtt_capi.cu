@@ -228,6 +228,7 @@ static void set_w_bytes(gtt_plan_s *P, const void *W) {
 extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
     if (!P || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or W");
     set_w_bytes(P, W);
+    if (P->precision == GTT_PREC_BF16X3) return tc_upload_w(P);
     return GTT_OK;
 }
 
@@ -378,11 +379,28 @@ extern "C" gtt_status_t gtt_plan_check(gtt_plan_t P) {
 extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
     if (precision == GTT_PREC_AUTO || precision == GTT_PREC_FP32) {
+        if (P->precision == GTT_PREC_BF16X3) {  // back to the CUDA-core schedule
+            std::vector<PassPlan> passes;
+            gtt_status_t st = P->explicit_g.empty()
+                                  ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
+                                  : make_explicit_schedule(P, (int)P->explicit_g.size(), P->explicit_g.data(),
+                                                           P->explicit_r.data(), &passes);
+            if (st != GTT_OK) return st;
+            P->passes = passes;
+        }
         P->precision = precision;
         return GTT_OK;
     }
-    if (precision == GTT_PREC_BF16X3)
-        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 precision is not available in this build");
+    if (precision == GTT_PREC_BF16X3) {
+        std::vector<PassPlan> passes;
+        gtt_status_t st = make_tc_schedule(P, &passes);
+        if (st != GTT_OK) return st;
+        st = tc_upload_w(P);
+        if (st != GTT_OK) return st;
+        P->passes = passes;
+        P->precision = precision;
+        return GTT_OK;
+    }
     return set_error(GTT_ERR_INVALID_ARG, "unknown precision");
 }
 
@@ -441,7 +459,9 @@ gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, con
         const void *in = i == 0 ? x : (const void *)y;
         void *outp = y;
         gtt_status_t st;
-        if (pp.tma.on) {
+        if (pp.tc.on) {
+            st = tc_run(P, pp, &Wb == &P->Wa, in, outp, stream);
+        } else if (pp.tma.on) {
             st = tma_run(P, pp, Wb, in, outp, stream);
         } else {
             void *args[4] = {(void *)&in, (void *)&outp, (void *)&pp.params, (void *)Wb.data()};
@@ -560,11 +580,14 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                  "%s{\"kernel\": \"%s\", \"m0\": %d, \"g\": %d, \"r\": %lld, \"D\": %d, "
                  "\"tile_bytes\": %lld, \"tiles\": %lld, \"grid\": %d, \"block\": %d, \"smem\": %zu, "
                  "\"ctas_per_sm\": %d, \"vec_mode\": %d, \"tma\": %s, \"nbuf\": %d}",
-                 i ? ", " : "", t ? pp.tma.name.c_str() : pp.name.c_str(), pp.m0, pp.g, pp.r, pp.D,
-                 (long long)pp.params.tile_elems * P->es, pp.params.tiles, t ? pp.tma.grid : pp.grid,
-                 t ? kTmaThreads : pp.block, t ? pp.tma.smem : pp.smem,
-                 t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode, t ? "true" : "false",
-                 t ? pp.tma.params.nbuf : 0);
+                 i ? ", " : "",
+                 pp.tc.on ? pp.tc.name.c_str() : t ? pp.tma.name.c_str() : pp.name.c_str(), pp.m0, pp.g,
+                 pp.r, pp.D, (long long)pp.params.tile_elems * P->es, pp.params.tiles,
+                 pp.tc.on ? pp.tc.grid : t ? pp.tma.grid : pp.grid,
+                 pp.tc.on ? pp.tc.block : t ? kTmaThreads : pp.block,
+                 pp.tc.on ? pp.tc.smem : t ? pp.tma.smem : pp.smem,
+                 pp.tc.on ? pp.tc.ctas_per_sm : t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode,
+                 t ? "true" : "false", t ? pp.tma.params.nbuf : 0);
         s += tmp;
     }
     s += "]}";
@@ -576,6 +599,7 @@ extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
     if (!P) return GTT_OK;
     if (P->dstage) cudaFree(P->dstage);
     if (P->dev_err) cudaFree(P->dev_err);
+    if (P->d_wpieces) cudaFree(P->d_wpieces);
     if (P->ws_grad) cudaFree(P->ws_grad);
     if (P->ws_ck) cudaFree(P->ws_ck);
     if (P->ws_dw) cudaFree(P->ws_dw);

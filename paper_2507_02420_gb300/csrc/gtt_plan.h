@@ -31,6 +31,16 @@ struct TmaPass {
     CUtensorMap map_in, map_out;  // the type carries its own 64-byte alignment
 };
 
+// b = 16 tensor-core (BF16x3) variant of a pass (gtt_tc16.cuh).
+struct TcPass {
+    bool on = false;
+    int g = 0;
+    const void *kern = nullptr;
+    int grid = 0, block = 0, ctas_per_sm = 0;
+    size_t smem = 0;
+    std::string name;
+};
+
 struct PassPlan {
     int m0 = 0, g = 0, D = 1;
     long long r = 1;
@@ -40,6 +50,7 @@ struct PassPlan {
     size_t smem = 0;
     std::string name;  // kernel name with its template arguments
     TmaPass tma;
+    TcPass tc;
 };
 
 // One pass of the backward schedule: the tile geometry (one stage per digit),
@@ -93,6 +104,7 @@ struct gtt_plan_s {
     std::vector<int> explicit_g;         // explicit schedule (gtt_plan_set_passes), else empty
     std::vector<long long> explicit_r;
     int *dev_err = nullptr;              // device flag raised by a bounded wait that expired
+    void *d_wpieces = nullptr;           // BF16x3 pieces of W and W^T (b = 16 tensor-core path)
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
     std::vector<cudaEvent_t> event_pool;
@@ -112,6 +124,10 @@ bool tune_apply_cached(gtt_plan_s *P);
 gtt_status_t autotune(gtt_plan_s *P, int max_candidates);
 gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits, const long long *runs,
                                     std::vector<PassPlan> *out);
+// b = 16 tensor-core passes (gtt_tc16.cu)
+gtt_status_t tc_upload_w(gtt_plan_s *P);
+gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out);
+gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s);
 // Attach the TMA variant to a forward pass when its geometry allows (true if attached).
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,

@@ -1,0 +1,98 @@
+// Host side of the b = 16 tensor-core passes (gtt_tc16.cuh): the BF16x3
+// schedule, the split W operands, and the launch.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gtt_plan.h"
+#include "gtt_tc16.cuh"
+
+namespace gtt {
+
+// B operand: rows n = 16p + i hold piece p of row i of M (M = W for the
+// forward, W^T for the adjoint), K-major core-matrix layout, 48 x 16 BF16.
+static void split_w_pieces(const float *M, int transpose, unsigned char *out) {
+    memset(out, 0, 1536);
+    for (int n = 0; n < 48; ++n)
+        for (int k = 0; k < 16; ++k) {
+            const int p = n / 16, i = n % 16;
+            const float w = transpose ? M[k * 16 + i] : M[i * 16 + k];
+            const __nv_bfloat16 w0 = __float2bfloat16_rn(w);
+            const float r1 = w - __bfloat162float(w0);
+            const __nv_bfloat16 w1 = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(w1);
+            const __nv_bfloat16 w2 = __float2bfloat16_rn(r2);
+            const __nv_bfloat16 piece = p == 0 ? w0 : p == 1 ? w1 : w2;
+            const size_t off = (n / 8) * 256 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+            memcpy(out + off, &piece, 2);
+        }
+}
+
+gtt_status_t tc_upload_w(gtt_plan_s *P) {
+    if (!P->d_wpieces) {
+        cudaError_t e = cudaMalloc(&P->d_wpieces, 2 * 1536);
+        if (e != cudaSuccess) {
+            P->d_wpieces = nullptr;
+            return set_error(GTT_ERR_ALLOC, "BF16 weight pieces");
+        }
+    }
+    unsigned char host[2 * 1536];
+    const float *W = reinterpret_cast<const float *>(P->Wf.data());  // element layout prefix
+    split_w_pieces(W, 0, host);
+    split_w_pieces(W, 1, host + 1536);
+    cudaError_t e = cudaMemcpy(P->d_wpieces, host, sizeof host, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "uploading BF16 weight pieces");
+    return GTT_OK;
+}
+
+// Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (2, r=16)
+// passes, and a final (1, r=256) pass when one digit is left.
+gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
+    if (P->b != 16 || P->dtype != GTT_F32 || P->n < 3)
+        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 needs b = 16, FP32 and n >= 3");
+    const void *k = (const void *)&gtt_tc16_pass_kernel;
+    if (allow_max_smem(k, P->smem_optin) != cudaSuccess) return set_error(GTT_ERR_CUDA, "tc kernel attribute");
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, kTcSmemPerCta) != cudaSuccess ||
+        per_sm < 1)
+        return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
+    per_sm = std::min(per_sm, 4);  // 4 x 128 TMEM columns per SM
+    std::vector<PassPlan> passes;
+    int m0 = 0;
+    while (m0 < P->n) {
+        const int left = P->n - m0;
+        const int g = m0 == 0 ? 3 : (left >= 2 ? 2 : 1);
+        const long long r = m0 == 0 ? 1 : (g == 2 ? 16 : 256);
+        PassPlan pp;
+        gtt_status_t st = build_pass(P, m0, g, r, 1, &pp);
+        if (st != GTT_OK) return st;
+        pp.tc.on = true;
+        pp.tc.g = g;
+        pp.tc.kern = k;
+        pp.tc.grid = (int)std::min<long long>((long long)per_sm * P->num_sms, pp.params.tiles);
+        pp.tc.ctas_per_sm = per_sm;
+        pp.tc.block = kTcThreads;
+        pp.tc.smem = kTcSmemPerCta;
+        pp.tc.name = "gtt_tc16_pass_kernel<bf16x3,g=" + std::to_string(g) + ">";
+        passes.push_back(pp);
+        m0 += g;
+    }
+    *out = passes;
+    return GTT_OK;
+}
+
+gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s) {
+    TcParams tp;
+    memset(&tp, 0, sizeof(tp));
+    tp.p = pp.params;
+    tp.g = pp.tc.g;
+    tp.wpieces = (const unsigned char *)P->d_wpieces + (adjoint ? 1536 : 0);
+    tp.err = P->dev_err;
+    void *args[3] = {(void *)&in, (void *)&out, (void *)&tp};
+    return launch_timed(P, pp.tc.kern, dim3(pp.tc.grid), dim3(pp.tc.block), args, pp.tc.smem, s, pp.tc.name);
+}
+
+} // namespace gtt

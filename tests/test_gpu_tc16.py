@@ -1,0 +1,106 @@
+"""GPU parity of the b = 16 tensor-core path (BF16x3 splits, FP32 accumulate in
+tensor memory) against the FP64 oracle, and against the FP32 CUDA-core path."""
+import numpy as np
+import pytest
+import torch
+
+import gtt_inputs as gi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2507_02420_gb300 import build
+    build.build()
+    import paper_2507_02420_gb300 as g
+    torch.cuda.set_device(0)
+    return g
+
+
+def rel(a, ref):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("n,batch", [(3, 4), (4, 3), (5, 2), (6, 1)])
+def test_bf16x3_matches_oracle(g, n, batch):
+    rng = np.random.default_rng(9000 + n)
+    W = gi.haar_orthogonal(16, rng).astype(np.float32)
+    x = gi.normal_x((batch, 16 ** n), rng, np.float32)
+    plan = g.Plan(W, n, "f32", batch)
+    plan.set_precision(g.PREC_BF16X3)
+    d = plan.describe()
+    assert all("tc16" in p["kernel"] for p in d["passes"]), d
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    xr = plan.inverse(y)
+    torch.cuda.synchronize()
+    plan.check()
+    ref = oracle.modes(W.astype(np.float64), x.astype(np.float64))
+    e = rel(y.cpu().numpy(), ref)
+    print(f"bf16x3 b=16 n={n}: forward rel-L2 {e:.3e}")
+    assert e <= 1e-6
+    assert rel(xr.cpu().numpy(), x.astype(np.float64)) <= 2e-6
+
+
+def test_bf16x3_non_orthogonal_w_and_inverse_is_adjoint(g):
+    rng = np.random.default_rng(9100)
+    W = (rng.standard_normal((16, 16)) * 0.3).astype(np.float32)
+    x = gi.normal_x((2, 16 ** 4), rng, np.float32)
+    plan = g.Plan(W, 4, "f32", 2)
+    plan.set_precision(g.PREC_BF16X3)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    z = plan.inverse(y)
+    torch.cuda.synchronize()
+    ref = oracle.modes(W.astype(np.float64), x.astype(np.float64))
+    assert rel(y.cpu().numpy(), ref) <= 1e-6
+    assert rel(z.cpu().numpy(), oracle.adjoint(W.astype(np.float64), ref)) <= 1e-6
+
+
+def test_b16_n6_batch64_bf16x3_full_size_sampled(g):
+    """b=16, n=6, batch 64: BF16x3 tensor-core path, items 0, 21, 42, 63 vs the
+    oracle at rel-L2 <= 1e-6; the FP32 CUDA-core path on the same input too."""
+    W, x = gi.config_inputs(2)
+    plan = g.Plan(W, 6, "f32", 64)
+    plan.set_precision(g.PREC_BF16X3)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    torch.cuda.synchronize()
+    plan.check()
+    plan32 = g.Plan(W, 6, "f32", 64)
+    y32 = plan32.forward(xd)
+    torch.cuda.synchronize()
+    for item in (0, 21, 42, 63):
+        ref = oracle.modes(W.astype(np.float64), x[item].astype(np.float64))
+        e_tc, e_32 = rel(y[item].cpu().numpy(), ref), rel(y32[item].cpu().numpy(), ref)
+        print(f"item {item}: bf16x3 rel-L2 {e_tc:.3e}, fp32 rel-L2 {e_32:.3e}")
+        assert e_tc <= 1e-6 and e_32 <= 1e-6
+
+
+def test_bf16x3_repeatable_and_switchable(g):
+    rng = np.random.default_rng(9200)
+    W = gi.haar_orthogonal(16, rng).astype(np.float32)
+    x = gi.normal_x((3, 16 ** 4), rng, np.float32)
+    plan = g.Plan(W, 4, "f32", 3)
+    xd = torch.from_numpy(x).cuda()
+    plan.set_precision(g.PREC_BF16X3)
+    a = plan.forward(xd).cpu().numpy()
+    b = plan.forward(xd).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    plan.set_precision(g.PREC_FP32)
+    assert not any("tc16" in p["kernel"] for p in plan.describe()["passes"])
+    c = plan.forward(xd).cpu().numpy()
+    ref = oracle.modes(W.astype(np.float64), x.astype(np.float64))
+    assert rel(c, ref) <= 1e-6
+
+
+def test_bf16x3_rejected_where_unsupported(g):
+    rng = np.random.default_rng(9300)
+    for b, n, dt in ((8, 4, "f32"), (16, 2, "f32"), (16, 3, "c64")):
+        W = gi.haar_orthogonal(b, rng).astype(np.float32 if dt == "f32" else np.complex64)
+        plan = g.Plan(W, n, dt, 1)
+        with pytest.raises(g.GTTError) as ei:
+            plan.set_precision(g.PREC_BF16X3)
+        assert ei.value.status == 2
