@@ -375,29 +375,48 @@ def _time_device(fn, reps: int, warm: int = 3) -> float:
     return s.elapsed_time(e) / 1e3 / reps
 
 
-def run_extras(g, dev, peaks):
-    """The other hot-path rows, each timed on its own workload (not part of
-    `value`): the b=16 FP32 contraction path, the b=8 training step (forward +
-    hand-written backward) and the 1000-request grouped launch."""
+def extra_b16(g, dev, hbm, reps=10, batch=64):
+    """b = 16, n = 6, batch 64, FP32: CUDA-core path vs BF16x3 tensor-core path,
+    each with and without L2 chunking; errors against the FP64 GPU path.
+    (`batch` may shrink the batch for short profiler runs.)"""
     import torch
-    out = {}
-    hbm = float(peaks["hbm_gbs"])
-    # b = 16, n = 6, batch 64, FP32: CUDA-core contraction path
-    W2, x2 = gi.config_inputs(2)
-    p2 = g.Plan(W2, 6, "f32", 64)
+    W2, x2 = gi.config_inputs(2, batch=batch)
     x2d = torch.from_numpy(x2).to(dev)
     del x2
-    y2d = torch.empty_like(x2d)
-    t = _time_device(lambda: p2.forward(x2d, out=y2d), reps=10)
     n2 = x2d.numel()
-    out["b16_n6_batch64_f32"] = {
-        "path": "fp32_cuda_core", "ms": t * 1e3, "gelem_s": n2 / t / 1e9,
-        "passes": len(p2.describe()["passes"]),
-        "hbm_gbs_algorithmic": len(p2.describe()["passes"]) * 2 * n2 * 4 / t / 1e9,
-        "hbm_frac": len(p2.describe()["passes"]) * 2 * n2 * 4 / t / 1e9 / hbm}
-    del x2d, y2d, p2
+    res = {}
+    outs = {}
+    for name, prec in (("fp32_cuda_core", g.PREC_FP32), ("bf16x3_tcgen05", g.PREC_BF16X3)):
+        p2 = g.Plan(W2, 6, "f32", batch)
+        p2.set_precision(prec)
+        y2d = torch.empty_like(x2d)
+        for chunk in (0, -1):
+            p2.set_chunking(chunk)
+            t = _time_device(lambda: p2.forward(x2d, out=y2d), reps=reps)
+            passes = len(p2.describe()["passes"])
+            res[f"{name}{'_l2chunked' if chunk else ''}"] = {
+                "ms": t * 1e3, "gelem_s": n2 / t / 1e9, "passes": passes,
+                "hbm_frac_if_passes_from_hbm": passes * 2 * n2 * 4 / t / 1e9 / hbm}
+        p2.check()
+        outs[name] = y2d
+        del p2
+    # error of both paths against the FP64 GPU path (parity-tested against the
+    # FP64 CPU oracle at 1e-13), over the whole batch
+    p64 = g.Plan(W2.astype(np.float64), 6, "f64", batch)
+    y64 = p64.forward(x2d.double())
+    for name, y in outs.items():
+        res[name]["rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(y.double() - y64) /
+                                            torch.linalg.vector_norm(y64))
+    best = lambda k: min(v["ms"] for kk, v in res.items() if kk.startswith(k))  # noqa: E731
+    res["bf16x3_speedup_over_fp32"] = best("fp32_cuda_core") / best("bf16x3_tcgen05")
+    del x2d, outs, y64, p64
     torch.cuda.empty_cache()
-    # b = 8, n = 7, batch 32, FP32 training step: forward + backward (dx, dW)
+    return res
+
+
+def extra_train(g, dev, hbm, reps=10):
+    """b = 8, n = 7, batch 32, FP32 training step: forward + backward (dx, dW)."""
+    import torch
     W3, x3 = gi.config_inputs(3)
     p3 = g.Plan(W3, 7, "f32", 32)
     x3d = torch.from_numpy(x3).to(dev)
@@ -407,12 +426,22 @@ def run_extras(g, dev, peaks):
     def train_step():
         p3.forward(x3d, out=y3d)
         p3.backward(x3d, dy3)
-    t = _time_device(train_step, reps=10)
-    out["b8_n7_batch32_train_step"] = {"ms": t * 1e3, "gelem_s": x3d.numel() / t / 1e9,
-                                       "includes": "gtt_forward + gtt_backward (dx and dW)"}
+    t = _time_device(train_step, reps=reps)
+    p3.set_chunking(-1)
+    tc = _time_device(lambda: p3.forward(x3d, out=y3d), reps=reps)
+    p3.set_chunking(0)
+    tf = _time_device(lambda: p3.forward(x3d, out=y3d), reps=reps)
+    res = {"ms": t * 1e3, "gelem_s": x3d.numel() / t / 1e9,
+           "includes": "gtt_forward + gtt_backward (dx and dW)",
+           "forward_ms": tf * 1e3, "forward_l2chunked_ms": tc * 1e3}
     del x3d, y3d, dy3, p3
     torch.cuda.empty_cache()
-    # 1000 uneven requests in one persistent launch (CUDA graph)
+    return res
+
+
+def extra_grouped(g, dev, hbm, reps=10):
+    """1000 uneven requests in one persistent launch (CUDA graph)."""
+    import torch
     reqs = []
     elems = 0
     nbytes = 0
@@ -423,13 +452,27 @@ def run_extras(g, dev, peaks):
         elems += x.size
         nbytes += x.nbytes
     grp = g.Group(reqs)
-    t = _time_device(grp.execute, reps=10)
+    t = _time_device(grp.execute, reps=reps)
     grp.check()
     d = grp.describe()
-    out["grouped_1000_uneven"] = {
-        "ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
-        "kernel_launches_per_execute": 1, "work_items": d["work_items"],
-        "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9}
+    return {"ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
+            "kernel_launches_per_execute": 1, "work_items": d["work_items"],
+            "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9}
+
+
+EXTRAS = {"b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_train_step", extra_train),
+          "grouped": ("grouped_1000_uneven", extra_grouped)}
+
+
+def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64):
+    """The other hot-path rows, each timed on its own workload (not part of
+    `value`): the b=16 contraction on both paths, the b=8 training step
+    (forward + hand-written backward) and the 1000-request grouped launch."""
+    hbm = float(peaks["hbm_gbs"])
+    out = {}
+    for key, (name, fn) in EXTRAS.items():
+        if only is None or key == only:
+            out[name] = fn(g, dev, hbm, reps, b16_batch) if key == "b16" else fn(g, dev, hbm, reps)
     return out
 
 
@@ -443,6 +486,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-row measurements of the other workloads")
+    ap.add_argument("--only", choices=sorted(EXTRAS), default=None,
+                    help="run only this extra workload (a few repetitions) and print its JSON; "
+                         "used for short profiler runs")
+    ap.add_argument("--b16-batch", type=int, default=64,
+                    help="batch of the b=16 extra (smaller for profiler runs)")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -456,6 +504,16 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank)
 
+    if args.only:
+        import torch
+
+        import paper_2507_02420_gb300 as g
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        peaks, _ = measured_peaks()
+        print(json.dumps(run_extras(g, dev, peaks, only=args.only, reps=max(1, args.steps),
+                                    b16_batch=args.b16_batch)), flush=True)
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist

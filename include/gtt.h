@@ -151,6 +151,17 @@ gtt_status_t gtt_autotune_cache_save(const char *path);
 gtt_status_t gtt_plan_set_pipeline(gtt_plan_t plan, int use_tma, int nbuf);
 
 /*
+ * gtt_plan_set_chunking -- run every pass on `items` batch items at a time
+ * before moving to the next items, so that the passes after the first read
+ * the previous pass's output from L2 instead of HBM (useful when one item is
+ * small enough for L2 but the batch is not).  0 = whole batch per pass (the
+ * default); -1 = automatic (chunks of at most 48 MiB when the batch is larger
+ * than 96 MiB and an item is at most 96 MiB, else off).  Results are
+ * identical; only the launch order changes (passes x chunks launches).
+ */
+gtt_status_t gtt_plan_set_chunking(gtt_plan_t plan, long long items);
+
+/*
  * gtt_plan_check -- wait for the device and report whether any kernel of this
  * plan gave up a bounded wait (GTT_ERR_TIMEOUT; the flag is then cleared).
  * Kernels never spin without limit: an expired wait records the error, drains

@@ -29,6 +29,7 @@ SIGNATURES = {
     "gtt_autotune_cache_load": (_I, [ctypes.c_char_p]),
     "gtt_autotune_cache_save": (_I, [ctypes.c_char_p]),
     "gtt_plan_check": (_I, [_P]),
+    "gtt_plan_set_chunking": (_I, [_P, _LL]),
     "gtt_forward": (_I, [_P, _P, _P, _P]),
     "gtt_inverse": (_I, [_P, _P, _P, _P]),
     "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),

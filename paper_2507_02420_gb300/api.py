@@ -115,6 +115,10 @@ class Plan:
         check(self._lib.gtt_plan_set_pipeline(self._h, int(bool(use_tma)), int(nbuf)),
               "gtt_plan_set_pipeline")
 
+    def set_chunking(self, items: int = -1):
+        """Run all passes on `items` batch items at a time (-1 automatic, 0 off)."""
+        check(self._lib.gtt_plan_set_chunking(self._h, int(items)), "gtt_plan_set_chunking")
+
     def check(self):
         """Raise GTTError(GTT_ERR_TIMEOUT) if a kernel of this plan gave up a bounded wait."""
         check(self._lib.gtt_plan_check(self._h), "gtt_plan_check")

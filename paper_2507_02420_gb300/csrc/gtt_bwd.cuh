@@ -68,7 +68,7 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
 #pragma unroll
         for (int j = 0; j < B; ++j) acc[i][j] = zero_<T>();
 
-    for (long long t = blockIdx.x; t < p.tiles; t += gridDim.x) {
+    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles; t += gridDim.x) {
         const long long hi = t / p.lo_blocks;
         const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
         const long long base = hi * LM + (long long)lob * r;

@@ -364,6 +364,17 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     return GTT_OK;
 }
 
+extern "C" gtt_status_t gtt_plan_set_chunking(gtt_plan_t P, long long items) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (items < -1) return set_error(GTT_ERR_INVALID_ARG, "items must be >= -1");
+    if (items == -1) {  // automatic: chunks of at most ~48 MiB when the batch exceeds ~96 MiB
+        const long long item_bytes = P->N * P->es, budget = 48ll << 20;
+        items = (P->total * P->es > 2 * budget && item_bytes <= 2 * budget) ? std::max(1ll, budget / item_bytes) : 0;
+    }
+    P->chunk_items = items;
+    return GTT_OK;
+}
+
 extern "C" gtt_status_t gtt_plan_check(gtt_plan_t P) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
     int flag = 0;
@@ -454,20 +465,34 @@ gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block
 // Launch every pass of the schedule with the given W bytes.
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream) {
-    for (size_t i = 0; i < P->passes.size(); ++i) {
-        PassPlan &pp = P->passes[i];
-        const void *in = i == 0 ? x : (const void *)y;
-        void *outp = y;
-        gtt_status_t st;
-        if (pp.tc.on) {
-            st = tc_run(P, pp, &Wb == &P->Wa, in, outp, stream);
-        } else if (pp.tma.on) {
-            st = tma_run(P, pp, Wb, in, outp, stream);
-        } else {
-            void *args[4] = {(void *)&in, (void *)&outp, (void *)&pp.params, (void *)Wb.data()};
-            st = launch_timed(P, pp.kern, dim3(pp.grid), dim3(pp.block), args, pp.smem, stream, pp.name);
+    // With chunking, every pass of a chunk of batch items runs before the next
+    // chunk starts, so the intermediate passes of a chunk read what the
+    // previous pass left in L2.  A batch item's tiles are consecutive in every
+    // pass, so a chunk is a tile range.
+    const long long citems = (P->chunk_items > 0 && P->chunk_items < P->batch) ? P->chunk_items : P->batch;
+    for (long long c0 = 0; c0 < P->batch; c0 += citems) {
+        const long long c1 = std::min(P->batch, c0 + citems);
+        for (size_t i = 0; i < P->passes.size(); ++i) {
+            PassPlan &pp = P->passes[i];
+            const long long per_item = pp.params.tiles / P->batch;
+            const long long tb = c0 * per_item, te = c1 * per_item;
+            const void *in = i == 0 ? x : (const void *)y;
+            void *outp = y;
+            gtt_status_t st;
+            if (pp.tc.on) {
+                st = tc_run(P, pp, &Wb == &P->Wa, in, outp, stream, tb, te);
+            } else if (pp.tma.on) {
+                st = tma_run(P, pp, Wb, in, outp, stream, tb, te);
+            } else {
+                PassParams prm = pp.params;
+                prm.tile_begin = tb;
+                prm.tiles = te;
+                const int grid = (int)std::min<long long>(pp.grid, te - tb);
+                void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)Wb.data()};
+                st = launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
+            }
+            if (st != GTT_OK) return st;
         }
-        if (st != GTT_OK) return st;
     }
     return GTT_OK;
 }

@@ -33,7 +33,8 @@ constexpr int kPassMaxThreads = 512;
 struct PassParams {
     long long total;      // batch * N elements
     long long L;          // b^m0: stride of the first transformed digit
-    long long tiles;      // total / (M * r)
+    long long tiles;      // end of the tile range of this launch (total / (M * r) for a whole pass)
+    long long tile_begin; // first tile of this launch (0 for a whole pass)
     uint32_t r;           // run length
     uint32_t M;           // b^g
     uint32_t tile_elems;  // M * r
@@ -155,7 +156,7 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
     const uint32_t tile_elems = p.tile_elems, r = p.r;
     const long long LM = p.L * (long long)p.M;
 
-    for (long long t = blockIdx.x; t < p.tiles; t += gridDim.x) {
+    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles; t += gridDim.x) {
         const long long hi = t / p.lo_blocks;
         const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
         const long long base = hi * LM + (long long)lob * r;

@@ -11,7 +11,7 @@ namespace gtt {
 // Default fixed-rule schedule: tiles of at most this many bytes (several CTAs
 // per SM) and runs of at least this many contiguous bytes in strided passes.
 constexpr long long kDefaultTileBytes = 48 * 1024;
-constexpr long long kDefaultRunBytes = 128;
+constexpr long long kDefaultRunBytes = 64;
 
 // One pass of a schedule: modes [m0, m0+g) with runs of r elements, register
 // windows of D digits, and its launch geometry.
@@ -105,6 +105,7 @@ struct gtt_plan_s {
     std::vector<long long> explicit_r;
     int *dev_err = nullptr;              // device flag raised by a bounded wait that expired
     void *d_wpieces = nullptr;           // BF16x3 pieces of W and W^T (b = 16 tensor-core path)
+    long long chunk_items = 0;           // batch items per L2-resident chunk (0: whole batch)
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
     std::vector<cudaEvent_t> event_pool;
@@ -127,11 +128,12 @@ gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits,
 // b = 16 tensor-core passes (gtt_tc16.cu)
 gtt_status_t tc_upload_w(gtt_plan_s *P);
 gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out);
-gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s);
+gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s,
+                    long long tile_begin, long long tile_end);
 // Attach the TMA variant to a forward pass when its geometry allows (true if attached).
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
-                     void *out, cudaStream_t stream);
+                     void *out, cudaStream_t stream, long long tile_begin, long long tile_end);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
 } // namespace gtt

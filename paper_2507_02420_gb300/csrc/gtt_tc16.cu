@@ -84,15 +84,19 @@ gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
     return GTT_OK;
 }
 
-gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s) {
+gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s,
+                    long long tile_begin, long long tile_end) {
     TcParams tp;
     memset(&tp, 0, sizeof(tp));
     tp.p = pp.params;
+    tp.p.tile_begin = tile_begin;
+    tp.p.tiles = tile_end;
+    const int grid = (int)std::min<long long>(pp.tc.grid, tile_end - tile_begin);
     tp.g = pp.tc.g;
     tp.wpieces = (const unsigned char *)P->d_wpieces + (adjoint ? 1536 : 0);
     tp.err = P->dev_err;
     void *args[3] = {(void *)&in, (void *)&out, (void *)&tp};
-    return launch_timed(P, pp.tc.kern, dim3(pp.tc.grid), dim3(pp.tc.block), args, pp.tc.smem, s, pp.tc.name);
+    return launch_timed(P, pp.tc.kern, dim3(grid), dim3(pp.tc.block), args, pp.tc.smem, s, pp.tc.name);
 }
 
 } // namespace gtt

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const floa
     const uint32_t blk = warp >> 2;  // M block (TMEM column range) of this warp
     const uint32_t lane_base = (warp & 3u) * 32u;
 
-    for (long long t = blockIdx.x; t < p.tiles && !failed; t += gridDim.x) {
+    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles && !failed; t += gridDim.x) {
         const long long hi = t / p.lo_blocks;
         const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
         const long long gbase = hi * LM + (long long)lob * r;

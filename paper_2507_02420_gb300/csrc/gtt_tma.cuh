@@ -36,7 +36,8 @@ __host__ __device__ constexpr int tma_min_blocks(int es, int B, int D) {
 }
 
 struct TmaParams {
-    long long tiles;
+    long long tiles;          // end of this launch's tile range
+    long long tile_begin;     // first tile of this launch's range
     uint32_t M, r, tile_elems, lo_blocks, tile_bytes;
     uint32_t rows_per_box;    // rows per TMA box (<= 256)
     uint32_t boxes_per_cb;    // boxes per column block
@@ -137,8 +138,8 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
     const uint32_t bars = sbase_s + (uint32_t)p.nbuf * p.tile_bytes;  // nbuf mbarriers (8 bytes each)
 
     const uint32_t tid = threadIdx.x, nth = blockDim.x;
-    const long long my_tiles =
-        blockIdx.x < p.tiles ? (p.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long range = p.tiles - p.tile_begin;
+    const long long my_tiles = blockIdx.x < range ? (range - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (tid == 0) {
         for (int i = 0; i < p.nbuf; ++i) mbar_init(bars + 8u * i, 1);
@@ -148,7 +149,7 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
 
     // issue the loads of local tile j into buffer j % nbuf (thread 0 only)
     auto issue_load = [&](long long j) {
-        const long long t = blockIdx.x + j * (long long)gridDim.x;
+        const long long t = p.tile_begin + blockIdx.x + j * (long long)gridDim.x;
         const int buf = (int)(j % p.nbuf);
         const uint32_t bar = bars + 8u * buf;
         const uint32_t dst = sbase_s + (uint32_t)buf * p.tile_bytes;
@@ -169,7 +170,7 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
         }
     };
     auto issue_store = [&](long long j) {
-        const long long t = blockIdx.x + j * (long long)gridDim.x;
+        const long long t = p.tile_begin + blockIdx.x + j * (long long)gridDim.x;
         const uint32_t src = sbase_s + (uint32_t)(j % p.nbuf) * p.tile_bytes;
         if constexpr (CONTIG) {
             const long long row0 = t * (long long)(p.tile_bytes >> 7);

@@ -39,6 +39,7 @@ bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf) {
     TmaParams t;
     memset(&t, 0, sizeof(t));
     t.tiles = cp.tiles;
+    t.tile_begin = cp.tile_begin;
     t.M = cp.M;
     t.r = cp.r;
     t.tile_elems = cp.tile_elems;
@@ -127,7 +128,7 @@ static gtt_status_t encode(gtt_plan_s *P, const PassPlan &pp, const void *ptr, C
 }
 
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in, void *out,
-                     cudaStream_t stream) {
+                     cudaStream_t stream, long long tile_begin, long long tile_end) {
     TmaPass &tp = pp.tma;
     gtt_status_t st;
     if (tp.map_in_ptr != in) {
@@ -142,8 +143,11 @@ gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned cha
     }
     TmaParams prm = tp.params;
     prm.err = P->dev_err;
+    prm.tile_begin = tile_begin;
+    prm.tiles = tile_end;
+    const int grid = (int)std::min<long long>(tp.grid, tile_end - tile_begin);
     void *args[4] = {(void *)&tp.map_in, (void *)&tp.map_out, (void *)&prm, (void *)Wb.data()};
-    return launch_timed(P, tp.kern, dim3(tp.grid), dim3(kTmaThreads), args, tp.smem, stream, tp.name);
+    return launch_timed(P, tp.kern, dim3(grid), dim3(kTmaThreads), args, tp.smem, stream, tp.name);
 }
 
 } // namespace gtt
