@@ -68,10 +68,9 @@ gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
         bp.smem = bwd_smem_bytes(b, g, ipow_ll(b, g) * r, es, cplx);
         if (bp.smem > 227 * 1024) return set_error(GTT_ERR_UNSUPPORTED, "backward tile exceeds shared memory");
         cudaError_t e;
-        if (bp.smem > 48 * 1024) {
-            e = allow_max_smem(bk, P->smem_optin);
-            if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute (backward)");
-        }
+        e = allow_max_smem(bk, P->smem_optin);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(bk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute (backward)");
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bk, kBwdThreads, bp.smem);
         if (e != cudaSuccess) return cuda_error(e, "occupancy query (backward)");

@@ -95,10 +95,9 @@ gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPl
     pp.smem = (pp.smem + 15) / 16 * 16;
     if (pp.smem > 227 * 1024) return set_error(GTT_ERR_INTERNAL, "tile exceeds shared memory");
     cudaError_t e;
-    if (pp.smem > 48 * 1024) {
-        e = allow_max_smem(pp.kern, P->smem_optin);
-        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
-    }
+    e = allow_max_smem(pp.kern, P->smem_optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pp.kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pp.kern, pp.block, pp.smem);
     if (e != cudaSuccess) return cuda_error(e, "occupancy query");

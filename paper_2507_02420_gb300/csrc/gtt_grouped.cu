@@ -172,7 +172,9 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, G->device);
     if (G->smem > (size_t)optin) return fail(G, set_error(GTT_ERR_UNSUPPORTED, "group tiles exceed shared memory"));
     const void *k = (const void *)&gtt_grouped_kernel;
-    if (allow_max_smem(k, optin) != cudaSuccess) return fail(G, set_error(GTT_ERR_CUDA, "group kernel attribute"));
+    if (allow_max_smem(k, optin) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        return fail(G, set_error(GTT_ERR_CUDA, "group kernel attribute"));
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGroupThreads, G->smem);
     if (e != cudaSuccess || per_sm < 1) return fail(G, set_error(GTT_ERR_UNSUPPORTED, "group kernel cannot be resident"));

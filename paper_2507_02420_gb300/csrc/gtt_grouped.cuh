@@ -134,7 +134,7 @@ __device__ __forceinline__ void group_dispatch(const GroupReq &rq, const GroupPa
     }
 }
 
-__global__ void __launch_bounds__(kGroupThreads) gtt_grouped_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(kGroupThreads, 2) gtt_grouped_kernel(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
     __shared__ int s_seg;

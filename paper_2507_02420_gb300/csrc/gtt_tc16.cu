@@ -54,12 +54,21 @@ gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
     if (P->b != 16 || P->dtype != GTT_F32 || P->n < 3)
         return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 needs b = 16, FP32 and n >= 3");
     const void *k = (const void *)&gtt_tc16_pass_kernel;
-    if (allow_max_smem(k, P->smem_optin) != cudaSuccess) return set_error(GTT_ERR_CUDA, "tc kernel attribute");
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, kTcSmemPerCta) != cudaSuccess ||
-        per_sm < 1)
-        return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
-    per_sm = std::min(per_sm, 4);  // 4 x 128 TMEM columns per SM
+    if (allow_max_smem(k, P->smem_optin) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        return set_error(GTT_ERR_CUDA, "tc kernel attribute");
+    // residency from the register and shared-memory budgets (the occupancy
+    // query under-reports kernels that allocate tensor memory), capped by the
+    // 4 x 128 TMEM columns of an SM
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return set_error(GTT_ERR_CUDA, "tc kernel attributes");
+    int regs_per_sm = 0, smem_per_sm = 0;
+    cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, P->device);
+    cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device);
+    const int by_regs = regs_per_sm / std::max(1, fa.numRegs * kTcThreads);
+    const int by_smem = smem_per_sm / (int)(kTcSmemPerCta + 1024);
+    int per_sm = std::min(std::min(by_regs, by_smem), 4);
+    if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
     std::vector<PassPlan> passes;
     int m0 = 0;
     while (m0 < P->n) {

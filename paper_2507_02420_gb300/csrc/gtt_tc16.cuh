@@ -31,7 +31,7 @@ namespace gtt {
 constexpr int kTcThreads = 256;
 constexpr int kTcTile = 4096;
 constexpr uint32_t kTcTmemCols = 128;       // two M blocks x 64 columns (48 used)
-constexpr size_t kTcSmemPerCta = 57344;      // caps residency at 4 CTAs/SM (4 x 128 TMEM columns)
+constexpr size_t kTcSmemPerCta = 65536;      // two fp32 tiles, three BF16 pieces, W pieces: 3 CTAs/SM
 
 struct TcParams {
     PassParams p;              // tile geometry: tile_elems = 4096, r = 16^(3-g)
@@ -84,8 +84,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const floa
     const uint32_t raw = smem_addr(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     unsigned char *base = smem_raw + pad;
-    float *S = reinterpret_cast<float *>(base);                        // 4096 + 256 floats
-    unsigned char *A = base + 17408;                                   // 3 pieces x 8 KiB
+    float *S0 = reinterpret_cast<float *>(base);                       // two tiles of 4096 + 256 floats
+    float *S1 = reinterpret_cast<float *>(base + 17408);
+    unsigned char *A = base + 2 * 17408;                               // 3 pieces x 8 KiB
     unsigned char *Bw = A + 3 * 8192;                                  // 1536 bytes
     uint64_t *bar = reinterpret_cast<uint64_t *>(Bw + 1536);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(Bw + 1536 + 8);
@@ -117,18 +118,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const floa
     const uint32_t blk = warp >> 2;  // M block (TMEM column range) of this warp
     const uint32_t lane_base = (warp & 3u) * 32u;
 
-    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles && !failed; t += gridDim.x) {
+    // asynchronous copy of tile t into the padded buffer Sb (one commit group)
+    auto issue_load = [&](long long t, float *Sb) {
+        const long long hi = t / p.lo_blocks;
+        const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
+        const long long gb = hi * LM + (long long)lob * r;
+        for (uint32_t c = tid; c < kTcTile / 4; c += kTcThreads) {
+            // 4 consecutive elements: same row (r in {1, 16, 256}), same 16-element pad group
+            const uint32_t e = c * 4, row = p.div_r.div(e), col = e - row * r;
+            const float *src = in + gb + (long long)row * p.L + col;
+            const uint32_t dst = smem_addr(&Sb[tc_spos(e)]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * i), "l"(src + i) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    int buf = 0;
+    if (p.tile_begin + blockIdx.x < p.tiles) issue_load(p.tile_begin + blockIdx.x, S0);
+    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles && !failed; t += gridDim.x, buf ^= 1) {
+        float *S = buf ? S1 : S0;
         const long long hi = t / p.lo_blocks;
         const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
         const long long gbase = hi * LM + (long long)lob * r;
-        // ---- HBM -> S (16-byte loads: r in {1, 16, 256}, L a power of 16)
-        for (uint32_t c = tid; c < kTcTile / 4; c += kTcThreads) {
-            const uint32_t e = c * 4, row = p.div_r.div(e), col = e - row * r;
-            const float4 v = *reinterpret_cast<const float4 *>(in + gbase + (long long)row * p.L + col);
-            S[tc_spos(e)] = v.x;
-            S[tc_spos(e + 1)] = v.y;
-            S[tc_spos(e + 2)] = v.z;
-            S[tc_spos(e + 3)] = v.w;
+        // prefetch the next tile into the other buffer, then wait for this one
+        if (t + gridDim.x < p.tiles) {
+            issue_load(t + gridDim.x, buf ? S0 : S1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
 
@@ -209,6 +228,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const floa
         }
         __syncthreads();
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves
     if (failed && tid == 0) atomicExch(tp.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
