@@ -210,23 +210,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const floa
             tmem_ld16(taddr + 16u, c1);
             tmem_ld16(taddr + 32u, c2);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (d < 2) {
 #pragma unroll
-            for (int n = 0; n < 16; ++n) S[tc_spos(e0 + n * sd)] = (c2[n] + c1[n]) + c0[n];
+                for (int n = 0; n < 16; ++n) S[tc_spos(e0 + n * sd)] = (c2[n] + c1[n]) + c0[n];
+            } else {
+                // last mode (digit h2): element m + 256 n sits at row (m/r) + n (256/r),
+                // column m % r; across a warp the stores are contiguous runs
+                const uint32_t rowm = p.div_r.div(m), colm = m - rowm * r;
+                const long long stride_n = (long long)(256u / r) * p.L;
+                float *o = out + gbase + (long long)rowm * p.L + colm;
+#pragma unroll
+                for (int n = 0; n < 16; ++n) o[n * stride_n] = (c2[n] + c1[n]) + c0[n];
+            }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
         if (failed) break;
-        // ---- S -> HBM
-        for (uint32_t c = tid; c < kTcTile / 4; c += kTcThreads) {
-            const uint32_t e = c * 4, row = p.div_r.div(e), col = e - row * r;
-            float4 v;
-            v.x = S[tc_spos(e)];
-            v.y = S[tc_spos(e + 1)];
-            v.z = S[tc_spos(e + 2)];
-            v.w = S[tc_spos(e + 3)];
-            *reinterpret_cast<float4 *>(out + gbase + (long long)row * p.L + col) = v;
-        }
-        __syncthreads();
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves
     if (failed && tid == 0) atomicExch(tp.err, 1);

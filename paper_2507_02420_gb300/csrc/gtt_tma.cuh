@@ -49,8 +49,19 @@ struct TmaParams {
     int stage_mask[kMaxStages];
     uint32_t stage_Ba[kMaxStages];  // b^a of the stage's window start a
     FastDiv stage_divBa[kMaxStages];
+    int stage_addr[kMaxStages];       // address form of the stage (kAddr*)
+    uint32_t stage_stride[kMaxStages];  // bytes between register elements (kAddrStride)
     int *err;  // device flag: 1 = an mbarrier wait expired
 };
+
+// How a stage's register elements map to swizzled shared memory (chosen on
+// the host from the tile geometry):
+//   kAddrGeneral  any layout: the full swizzle formula per element;
+//   kAddrStride   the swizzle phase (row mod 8) and the byte in the row are the
+//                 same for every element: a fixed byte stride;
+//   kAddrRowXor   element q sits q rows after a row that is a multiple of 8, at
+//                 the same byte: the 16-byte chunk index is XORed with q mod 8.
+constexpr int kAddrGeneral = 0, kAddrStride = 1, kAddrRowXor = 2;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -238,13 +249,36 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
                         continue;
                     }
                 }
+                const int form = p.stage_addr[st];
+                if (form == kAddrStride) {
+                    unsigned char *a0 = tb + Tile::off(row0, col, p.M);
+                    const uint32_t stride = p.stage_stride[st];
 #pragma unroll
-                for (int q = 0; q < RB; ++q)
-                    v[q] = *reinterpret_cast<const T *>(tb + Tile::off(row0 + q * Ba, col, p.M));
-                apply_window<T, B, D>(v, mask, W);
+                    for (int q = 0; q < RB; ++q) v[q] = *reinterpret_cast<const T *>(a0 + q * stride);
+                    apply_window<T, B, D>(v, mask, W);
 #pragma unroll
-                for (int q = 0; q < RB; ++q)
-                    *reinterpret_cast<T *>(tb + Tile::off(row0 + q * Ba, col, p.M)) = v[q];
+                    for (int q = 0; q < RB; ++q) *reinterpret_cast<T *>(a0 + q * stride) = v[q];
+                } else if (form == kAddrRowXor) {
+                    // swizzle row of element 0 (a multiple of 8) and its byte in the row
+                    const uint32_t off0 = Tile::off(row0, col, p.M);  // chunk phase 0 at q = 0
+                    unsigned char *rbase = tb + (off0 & ~127u) + (off0 & 15u);
+                    const uint32_t c = (off0 >> 4) & 7u;
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        v[q] = *reinterpret_cast<const T *>(rbase + q * 128 + (((c ^ (uint32_t)q) & 7u) << 4));
+                    apply_window<T, B, D>(v, mask, W);
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        *reinterpret_cast<T *>(rbase + q * 128 + (((c ^ (uint32_t)q) & 7u) << 4)) = v[q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        v[q] = *reinterpret_cast<const T *>(tb + Tile::off(row0 + q * Ba, col, p.M));
+                    apply_window<T, B, D>(v, mask, W);
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        *reinterpret_cast<T *>(tb + Tile::off(row0 + q * Ba, col, p.M)) = v[q];
+                }
             }
             __syncthreads();
         }

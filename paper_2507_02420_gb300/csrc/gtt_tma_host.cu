@@ -50,10 +50,33 @@ bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf) {
     t.div_lo_blocks = cp.div_lo_blocks;
     t.div_r = cp.div_r;
     t.nstages = cp.nstages;
+    const bool contig_tile = cp.L == 1;
+    const uint32_t R128 = 128 / es;
+    long long RB = 1;
+    for (int i = 0; i < pp->D; ++i) RB *= b;
     for (int s = 0; s < cp.nstages; ++s) {
+        const uint32_t Ba = cp.stage_divBa[s].d;
         t.stage_mask[s] = cp.stage_mask[s];
-        t.stage_Ba[s] = cp.stage_divBa[s].d;
+        t.stage_Ba[s] = Ba;
         t.stage_divBa[s] = cp.stage_divBa[s];
+        // address form (see kAddr* in gtt_tma.cuh); M % 8 == 0 is required below
+        t.stage_addr[s] = kAddrGeneral;
+        t.stage_stride[s] = 0;
+        if (!contig_tile) {
+            if (Ba % 8 == 0) {
+                t.stage_addr[s] = kAddrStride;
+                t.stage_stride[s] = Ba * 128u;
+            } else if (Ba == 1 && RB % 8 == 0) {
+                t.stage_addr[s] = kAddrRowXor;
+            }
+        } else if (Ba > 1) {
+            if (Ba % (8 * R128) == 0) {
+                t.stage_addr[s] = kAddrStride;
+                t.stage_stride[s] = Ba * (uint32_t)es;
+            } else if (Ba == R128 && RB % 8 == 0) {
+                t.stage_addr[s] = kAddrRowXor;
+            }
+        }
     }
     if (contig) {
         if (cp.r != 1) return false;  // contiguous tiles of the first pass only
