@@ -48,33 +48,42 @@ gtt_status_t tc_upload_w(gtt_plan_s *P) {
     return GTT_OK;
 }
 
-// Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (2, r=16)
-// passes, and a final (1, r=256) pass when one digit is left.
-gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
-    if (P->b != 16 || P->dtype != GTT_F32 || P->n < 3)
-        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 needs b = 16, FP32 and n >= 3");
-    const void *k = (const void *)&gtt_tc16_pass_kernel;
+static const void *tc_kernel(int g) {
+    return g == 3 ? (const void *)&gtt_tc16_pass_kernel<3>
+                  : g == 2 ? (const void *)&gtt_tc16_pass_kernel<2> : (const void *)&gtt_tc16_pass_kernel<1>;
+}
+
+// CTAs of a tensor-core pass kernel per SM, from the register and shared-memory
+// budgets (the occupancy query under-reports kernels that allocate tensor
+// memory), capped by the 4 x 128 TMEM columns of an SM; 0 on failure
+static int tc_residency(gtt_plan_s *P, const void *k) {
     if (allow_max_smem(k, P->smem_optin) != cudaSuccess ||
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-        return set_error(GTT_ERR_CUDA, "tc kernel attribute");
-    // residency from the register and shared-memory budgets (the occupancy
-    // query under-reports kernels that allocate tensor memory), capped by the
-    // 4 x 128 TMEM columns of an SM
+        return 0;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return set_error(GTT_ERR_CUDA, "tc kernel attributes");
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
     int regs_per_sm = 0, smem_per_sm = 0;
     cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, P->device);
     cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device);
     const int by_regs = regs_per_sm / std::max(1, fa.numRegs * kTcThreads);
     const int by_smem = smem_per_sm / (int)(kTcSmemPerCta + 1024);
-    int per_sm = std::min(std::min(by_regs, by_smem), 4);
-    if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
+    return std::min(std::min(by_regs, by_smem), 4);
+}
+
+// Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (2, r=16)
+// passes, and a final (1, r=256) pass when one digit is left.
+gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
+    if (P->b != 16 || P->dtype != GTT_F32 || P->n < 3)
+        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 needs b = 16, FP32 and n >= 3");
     std::vector<PassPlan> passes;
     int m0 = 0;
     while (m0 < P->n) {
         const int left = P->n - m0;
         const int g = m0 == 0 ? 3 : (left >= 2 ? 2 : 1);
         const long long r = m0 == 0 ? 1 : (g == 2 ? 16 : 256);
+        const void *k = tc_kernel(g);
+        const int per_sm = tc_residency(P, k);
+        if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, 1, &pp);
         if (st != GTT_OK) return st;

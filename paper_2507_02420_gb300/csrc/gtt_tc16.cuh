@@ -30,8 +30,13 @@ namespace gtt {
 
 constexpr int kTcThreads = 256;
 constexpr int kTcTile = 4096;
-constexpr uint32_t kTcTmemCols = 128;       // two M blocks x 64 columns (48 used)
-constexpr size_t kTcSmemPerCta = 65536;      // two fp32 tiles, three BF16 pieces, W pieces: 3 CTAs/SM
+constexpr int kTcBufs = 3;                   // tile ring: the tile in work and two prefetched
+constexpr uint32_t kTcTileBytes = kTcTile * 4;
+constexpr uint32_t kTcTmemCols = 128;        // two M blocks x 64 columns (48 used)
+constexpr uint32_t kTcPieceBytes = 8192;     // one BF16 piece of the A operand: 256 rows x 16
+constexpr uint32_t kTcWBytes = 1536;         // B operand: 48 rows x 16 BF16
+// ring, A pieces, B operand, mbarrier + TMEM slot, and slack for 128-byte alignment: 3 CTAs/SM
+constexpr size_t kTcSmemPerCta = kTcBufs * kTcTileBytes + 3 * kTcPieceBytes + kTcWBytes + 16 + 128;
 
 struct TcParams {
     PassParams p;              // tile geometry: tile_elems = 4096, r = 16^(3-g)
@@ -77,23 +82,165 @@ __device__ __forceinline__ uint32_t kmaj_off(uint32_t m, uint32_t k) {
     return (m >> 3) * 256u + (k >> 3) * 128u + (m & 7u) * 16u + (k & 7u) * 2u;
 }
 
-__device__ __forceinline__ uint32_t tc_spos(uint32_t e) { return e + (e >> 4); }
+// Tile buffer layout.  Element (h2, h1, h0) of a tile sits at float index
+//   256 h2 + 16 R + 4 ((h0 / 4) ^ (R / 2 mod 4)) + h0 mod 4,   R = h1 ^ (h2 mod 2):
+// rows of 16 are swapped in pairs on odd h2 and their 4-float chunks XOR-permuted.
+// Every 16-byte chunk of the tile stays 16 contiguous bytes (so the global
+// loads are 16-byte copies), and the fibres of all three modes are read and
+// written without bank conflicts: mode 0 (along h0) as 4 x 128-bit accesses
+// per thread, modes 1 and 2 as 32-bit accesses whose 32 lanes hit 32 banks.
+__device__ __forceinline__ uint32_t tc_pos(uint32_t h2, uint32_t h1, uint32_t h0) {
+    const uint32_t R = h1 ^ (h2 & 1u);
+    return h2 * 256u + R * 16u + ((((h0 >> 2) ^ (R >> 1)) & 3u) << 2) + (h0 & 3u);
+}
 
-__global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const float *in, float *out, TcParams tp) {
+// Float offsets of the 16 elements of fibre m for mode D (the fibre runs along
+// digit D; m enumerates the other two digits, lower digit first).  For D = 0
+// only off[0], off[4], off[8], off[12] are used: the starts of 4 chunks.
+template <int D>
+__device__ __forceinline__ void tc_fibre(uint32_t m, uint32_t (&off)[16]) {
+    if (D == 0) {
+        const uint32_t h1 = m & 15u, h2 = m >> 4;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) off[k] = tc_pos(h2, h1, (uint32_t)k);
+    } else if (D == 1) {
+        // with p = h2 mod 2: 16 (k ^ p) = 16 k + 16 p for even k and 16 k - 16 p
+        // for odd k, and the chunk term depends on k / 2 mod 4 only
+        const uint32_t h0 = m & 15u, h2 = m >> 4, p = h2 & 1u, c = h0 >> 2;
+        const uint32_t be = h2 * 256u + 16u * p + (h0 & 3u), bo = h2 * 256u - 16u * p + (h0 & 3u);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            off[k] = ((k & 1) ? bo : be) + 16u * (uint32_t)k + ((c ^ ((uint32_t)(k >> 1) & 3u)) << 2);
+    } else {
+        // R = h1 ^ (k mod 2); the chunk term uses R / 2 = h1 / 2 for both parities
+        const uint32_t h0 = m & 15u, h1 = m >> 4, c = h0 >> 2;
+        const uint32_t chunk = ((c ^ (h1 >> 1)) & 3u) << 2;
+        const uint32_t pe = 16u * h1 + chunk + (h0 & 3u), po = 16u * (h1 ^ 1u) + chunk + (h0 & 3u);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) off[k] = ((k & 1) ? po : pe) + 256u * (uint32_t)k;
+    }
+}
+
+struct TcCtx {
+    uint32_t m;            // fibre of this thread (= row of the A operand)
+    uint32_t tmem;         // base of the TMEM allocation (lane 0, first column)
+    uint32_t tmem_row;     // this thread's accumulator row: its lane, its M block's columns
+    uint32_t a_smem, bar;  // A operand pieces and the MMA-completion mbarrier (shared addresses)
+    uint64_t descB;
+    unsigned char *A;
+};
+
+// One mode of the tile in S: read fibre m, split it into three BF16 pieces
+// (the A operand), run the BF16x3 MMAs into TMEM, and write y_m back to S
+// (D < 2) or, for the last mode, straight to global memory at o[n * stride_n].
+// Returns false, uniformly across the CTA, if the MMA completion timed out.
+template <int D>
+__device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phase, float *o, long long stride_n) {
+    uint32_t off[16];
+    tc_fibre<D>(c.m, off);
+    float v[16];
+    if (D == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4 *>(S + off[4 * q]);
+            v[4 * q] = t.x, v[4 * q + 1] = t.y, v[4 * q + 2] = t.z, v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = S[off[k]];
+    }
+    // split into three BF16 pieces, written K-major (two 16-byte rows per piece);
+    // residuals x - piece are exact, formed as one packed FMA per pair
+    const float2 neg1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 x = make_float2(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(x.x, x.y);
+            const uint32_t u0 = *reinterpret_cast<const uint32_t *>(&p0);
+            const float2 r1 = __ffma2_rn(make_float2(__uint_as_float(u0 << 16), __uint_as_float(u0 & 0xFFFF0000u)), neg1, x);
+            const __nv_bfloat162 p1 = __floats2bfloat162_rn(r1.x, r1.y);
+            const uint32_t u1 = *reinterpret_cast<const uint32_t *>(&p1);
+            const float2 r2 = __ffma2_rn(make_float2(__uint_as_float(u1 << 16), __uint_as_float(u1 & 0xFFFF0000u)), neg1, r1);
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(r2.x, r2.y);
+            w0[q] = u0;
+            w1[q] = u1;
+            w2[q] = *reinterpret_cast<const uint32_t *>(&p2);
+        }
+        const uint32_t ko = kmaj_off(c.m, 8 * h);
+        *reinterpret_cast<uint4 *>(c.A + ko) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4 *>(c.A + kTcPieceBytes + ko) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4 *>(c.A + 2 * kTcPieceBytes + ko) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    }
+    fence_proxy_async();  // generic-proxy writes of A, visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (uint32_t b2 = 0; b2 < 2; ++b2) {
+            const uint32_t dcol = c.tmem + b2 * 64u;
+            const uint32_t aoff = c.a_smem + b2 * 4096u;  // rows 128 b2 .. (16 groups x 256 B)
+            umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(48), 0u);
+            umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(32), 1u);
+            umma_bf16(dcol + 32u, umma_sdesc(aoff + 2 * kTcPieceBytes), c.descB, umma_idesc(16), 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.bar)
+                     : "memory");
+    }
+    const bool ok = mbar_wait(c.bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float c0[16], c1[16], c2[16];
+    tmem_ld16(c.tmem_row, c0);
+    tmem_ld16(c.tmem_row + 16u, c1);
+    tmem_ld16(c.tmem_row + 32u, c2);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    float y[16];
+#pragma unroll
+    for (int n = 0; n < 16; n += 2) {
+        const float2 s = __fadd2_rn(__fadd2_rn(make_float2(c2[n], c2[n + 1]), make_float2(c1[n], c1[n + 1])),
+                                    make_float2(c0[n], c0[n + 1]));
+        y[n] = s.x, y[n + 1] = s.y;
+    }
+    if (D == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4 *>(S + off[4 * q]) = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+    } else if (D == 1) {
+#pragma unroll
+        for (int n = 0; n < 16; ++n) S[off[n]] = y[n];
+    } else {
+#pragma unroll
+        for (int n = 0; n < 16; ++n) o[n * stride_n] = y[n];
+    }
+    // the next mode issues MMAs into the same TMEM columns only after its own
+    // barrier, which every thread reaches after finishing these loads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (D < 2) __syncthreads();  // y_m in S, visible to the next mode
+    return true;
+}
+
+// Pass over tiles of three base-16 digits whose top G are transformed (G = 3:
+// contiguous tiles of the first pass; G = 2, 1: runs of r = 16, 256 elements).
+template <int G>
+__global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const float *in, float *out, TcParams tp) {
+    constexpr uint32_t kLogR = 4u * (3u - G);  // run length r = 16^(3-G)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
-    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
-    unsigned char *base = smem_raw + pad;
-    float *S0 = reinterpret_cast<float *>(base);                       // two tiles of 4096 + 256 floats
-    float *S1 = reinterpret_cast<float *>(base + 17408);
-    unsigned char *A = base + 2 * 17408;                               // 3 pieces x 8 KiB
-    unsigned char *Bw = A + 3 * 8192;                                  // 1536 bytes
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bw + 1536);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(Bw + 1536 + 8);
+    unsigned char *base = smem_raw + ((128u - (raw & 127u)) & 127u);
+    float *ring = reinterpret_cast<float *>(base);
+    unsigned char *A = base + kTcBufs * kTcTileBytes;
+    unsigned char *Bw = A + 3 * kTcPieceBytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bw + kTcWBytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(Bw + kTcWBytes + 8);
     const PassParams &p = tp.p;
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
 
-    for (uint32_t i = tid; i < 1536 / 16; i += kTcThreads)
+    for (uint32_t i = tid; i < kTcWBytes / 16; i += kTcThreads)
         reinterpret_cast<int4 *>(Bw)[i] = reinterpret_cast<const int4 *>(tp.wpieces)[i];
     if (tid == 0) {
         mbar_init(smem_addr(bar), 1);
@@ -108,124 +255,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) gtt_tc16_pass_kernel(const floa
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint64_t descB = umma_sdesc(smem_addr(Bw));
+    TcCtx c;
+    c.m = tid;  // fibre of this thread in every mode; warp w reads TMEM lanes 32 (w mod 4) ..
+    c.tmem = tmem;
+    c.tmem_row = tmem + (((warp & 3u) * 32u) << 16) + (warp >> 2) * 64u;
+    c.a_smem = smem_addr(A);
+    c.bar = smem_addr(bar);
+    c.descB = umma_sdesc(smem_addr(Bw));
+    c.A = A;
     uint32_t phase = 0;
     bool failed = false;
 
-    const uint32_t r = p.r;
     const long long LM = p.L * (long long)p.M;
-    const uint32_t m = tid;          // fibre of this thread in every mode
-    const uint32_t blk = warp >> 2;  // M block (TMEM column range) of this warp
-    const uint32_t lane_base = (warp & 3u) * 32u;
-
-    // asynchronous copy of tile t into the padded buffer Sb (one commit group)
-    auto issue_load = [&](long long t, float *Sb) {
+    const long long G0 = p.tile_begin + blockIdx.x, step = gridDim.x;
+    auto tile_base = [&](long long t) {
         const long long hi = t / p.lo_blocks;
         const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
-        const long long gb = hi * LM + (long long)lob * r;
-        for (uint32_t c = tid; c < kTcTile / 4; c += kTcThreads) {
-            // 4 consecutive elements: same row (r in {1, 16, 256}), same 16-element pad group
-            const uint32_t e = c * 4, row = p.div_r.div(e), col = e - row * r;
-            const float *src = in + gb + (long long)row * p.L + col;
-            const uint32_t dst = smem_addr(&Sb[tc_spos(e)]);
+        return hi * LM + ((long long)lob << kLogR);
+    };
+    // 16-byte copies of tile t into ring slot s (one commit group, empty past the end)
+    auto issue_load = [&](long long t, int s) {
+        if (t < p.tiles) {
+            const long long gb = tile_base(t);
+            float *Sb = ring + s * kTcTile;
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * i), "l"(src + i) : "memory");
+            for (int i = 0; i < kTcTile / 4 / kTcThreads; ++i) {
+                const uint32_t cc = tid + (uint32_t)i * kTcThreads, e = cc * 4u;
+                const uint32_t row = e >> kLogR, col = e & ((1u << kLogR) - 1u);
+                const float *src = in + gb + (long long)row * p.L + col;
+                const uint32_t dst = smem_addr(Sb + tc_pos(cc >> 6, (cc >> 2) & 15u, (cc & 3u) * 4u));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
-    int buf = 0;
-    if (p.tile_begin + blockIdx.x < p.tiles) issue_load(p.tile_begin + blockIdx.x, S0);
-    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles && !failed; t += gridDim.x, buf ^= 1) {
-        float *S = buf ? S1 : S0;
-        const long long hi = t / p.lo_blocks;
-        const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
-        const long long gbase = hi * LM + (long long)lob * r;
-        // prefetch the next tile into the other buffer, then wait for this one
-        if (t + gridDim.x < p.tiles) {
-            issue_load(t + gridDim.x, buf ? S0 : S1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
+    // last mode: element m + 256 n of the tile is row m / r + n (256 / r), column m mod r
+    const uint32_t rowm = c.m >> kLogR, colm = c.m & ((1u << kLogR) - 1u);
+    const long long stride_n = (long long)(256u >> kLogR) * p.L;
+    issue_load(G0, 0);
+    issue_load(G0 + step, 1);
+    int slot = 0;
+    for (long long t = G0; t < p.tiles; t += step) {
+        issue_load(t + 2 * step, slot == 0 ? 2 : slot - 1);
+        asm volatile("cp.async.wait_group 2;" ::: "memory");  // tile t's group is complete
         __syncthreads();
-
-        for (int d = 3 - tp.g; d < 3; ++d) {
-            // this thread's fibre: the other two hex digits (a < c) are m % 16, m / 16
-            const int a = d == 0 ? 1 : 0, c = d == 2 ? 1 : 2;
-            const uint32_t sd = 1u << (4 * d), sa = 1u << (4 * a), sc = 1u << (4 * c);
-            const uint32_t e0 = (m & 15u) * sa + (m >> 4) * sc;
-            float v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = S[tc_spos(e0 + k * sd)];
-            // split into three BF16 pieces, written K-major (two 16-byte rows per piece)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float xa = v[8 * h + 2 * q], xb = v[8 * h + 2 * q + 1];
-                    const __nv_bfloat162 p0 = __floats2bfloat162_rn(xa, xb);
-                    const float ra = xa - __low2float(p0), rb = xb - __high2float(p0);
-                    const __nv_bfloat162 p1 = __floats2bfloat162_rn(ra, rb);
-                    const float sa2 = ra - __low2float(p1), sb2 = rb - __high2float(p1);
-                    const __nv_bfloat162 p2 = __floats2bfloat162_rn(sa2, sb2);
-                    w0[q] = *reinterpret_cast<const uint32_t *>(&p0);
-                    w1[q] = *reinterpret_cast<const uint32_t *>(&p1);
-                    w2[q] = *reinterpret_cast<const uint32_t *>(&p2);
-                }
-                const uint32_t off = kmaj_off(m, 8 * h);
-                *reinterpret_cast<uint4 *>(A + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4 *>(A + 8192 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                *reinterpret_cast<uint4 *>(A + 16384 + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-            }
-            fence_proxy_async();
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (uint32_t b2 = 0; b2 < 2; ++b2) {
-                    const uint32_t dcol = tmem + b2 * 64u;
-                    const uint32_t aoff = smem_addr(A) + b2 * 4096u;  // rows 128*b2 .. (16 groups x 256 B)
-                    umma_bf16(dcol, umma_sdesc(aoff), descB, umma_idesc(48), 0u);
-                    umma_bf16(dcol + 16u, umma_sdesc(aoff + 8192u), descB, umma_idesc(32), 1u);
-                    umma_bf16(dcol + 32u, umma_sdesc(aoff + 16384u), descB, umma_idesc(16), 1u);
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_addr(bar))
-                             : "memory");
-            }
-            const bool ok = mbar_wait(smem_addr(bar), phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float c0[16], c1[16], c2[16];
-            const uint32_t taddr = tmem + (lane_base << 16) + blk * 64u;
-            tmem_ld16(taddr, c0);
-            tmem_ld16(taddr + 16u, c1);
-            tmem_ld16(taddr + 32u, c2);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (d < 2) {
-#pragma unroll
-                for (int n = 0; n < 16; ++n) S[tc_spos(e0 + n * sd)] = (c2[n] + c1[n]) + c0[n];
-            } else {
-                // last mode (digit h2): element m + 256 n sits at row (m/r) + n (256/r),
-                // column m % r; across a warp the stores are contiguous runs
-                const uint32_t rowm = p.div_r.div(m), colm = m - rowm * r;
-                const long long stride_n = (long long)(256u / r) * p.L;
-                float *o = out + gbase + (long long)rowm * p.L + colm;
-#pragma unroll
-                for (int n = 0; n < 16; ++n) o[n * stride_n] = (c2[n] + c1[n]) + c0[n];
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+        float *S = ring + slot * kTcTile;
+        float *o = out + tile_base(t) + (long long)rowm * p.L + colm;
+        bool ok = true;
+        if (G == 3) ok = tc_mode<0>(c, S, phase, o, stride_n);
+        if (G >= 2 && ok) ok = tc_mode<1>(c, S, phase, o, stride_n);
+        if (ok) ok = tc_mode<2>(c, S, phase, o, stride_n);
+        if (!ok) {
+            failed = true;
+            break;
         }
-        if (failed) break;
+        slot = slot == 2 ? 0 : slot + 1;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves
     if (failed && tid == 0) atomicExch(tp.err, 1);
