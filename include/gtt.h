@@ -151,15 +151,18 @@ gtt_status_t gtt_autotune_cache_save(const char *path);
 gtt_status_t gtt_plan_set_pipeline(gtt_plan_t plan, int use_tma, int nbuf);
 
 /*
- * gtt_plan_set_chunking -- run every pass on `items` batch items at a time
- * before moving to the next items, so that the passes after the first read
- * the previous pass's output from L2 instead of HBM (useful when one item is
- * small enough for L2 but the batch is not).  0 = whole batch per pass (the
- * default); -1 = automatic (chunks of at most 48 MiB when the batch is larger
- * than 96 MiB and an item is at most 96 MiB, else off).  Results are
- * identical; only the launch order changes (passes x chunks launches).
+ * gtt_plan_set_chunking -- L2-resident execution of the leading passes.  The
+ * leading passes of the schedule that only touch digits below some digit s
+ * (blocks of b^s consecutive elements, batch items included) run on chunks of
+ * at most `elems` elements (whole blocks) one chunk after the other, so each
+ * such pass after the first reads the previous pass's output from L2 instead
+ * of HBM; the remaining passes then run over all the data.  0 = off (the
+ * default); -1 = automatic (48 MiB chunks when the data exceed 96 MiB).  It
+ * takes effect only when at least two passes share a chunk.  Results are
+ * bitwise identical; only the launch order changes.  elems < -1 returns
+ * GTT_ERR_INVALID_ARG.
  */
-gtt_status_t gtt_plan_set_chunking(gtt_plan_t plan, long long items);
+gtt_status_t gtt_plan_set_chunking(gtt_plan_t plan, long long elems);
 
 /*
  * gtt_plan_check -- wait for the device and report whether any kernel of this

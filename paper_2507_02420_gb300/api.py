@@ -115,9 +115,10 @@ class Plan:
         check(self._lib.gtt_plan_set_pipeline(self._h, int(bool(use_tma)), int(nbuf)),
               "gtt_plan_set_pipeline")
 
-    def set_chunking(self, items: int = -1):
-        """Run all passes on `items` batch items at a time (-1 automatic, 0 off)."""
-        check(self._lib.gtt_plan_set_chunking(self._h, int(items)), "gtt_plan_set_chunking")
+    def set_chunking(self, elems: int = -1):
+        """Run the leading passes chunk by chunk, at most `elems` elements per
+        chunk, so that they pass data through L2 (-1 automatic, 0 off)."""
+        check(self._lib.gtt_plan_set_chunking(self._h, int(elems)), "gtt_plan_set_chunking")
 
     def check(self):
         """Raise GTTError(GTT_ERR_TIMEOUT) if a kernel of this plan gave up a bounded wait."""

@@ -363,14 +363,10 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     return GTT_OK;
 }
 
-extern "C" gtt_status_t gtt_plan_set_chunking(gtt_plan_t P, long long items) {
+extern "C" gtt_status_t gtt_plan_set_chunking(gtt_plan_t P, long long elems) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
-    if (items < -1) return set_error(GTT_ERR_INVALID_ARG, "items must be >= -1");
-    if (items == -1) {  // automatic: chunks of at most ~48 MiB when the batch exceeds ~96 MiB
-        const long long item_bytes = P->N * P->es, budget = 48ll << 20;
-        items = (P->total * P->es > 2 * budget && item_bytes <= 2 * budget) ? std::max(1ll, budget / item_bytes) : 0;
-    }
-    P->chunk_items = items;
+    if (elems < -1) return set_error(GTT_ERR_INVALID_ARG, "elems must be >= -1");
+    P->chunk_elems = elems;
     return GTT_OK;
 }
 
@@ -461,37 +457,70 @@ gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block
     return GTT_OK;
 }
 
+// L2-resident chunking for the current schedule.  Passes 0 .. prefix-1 only
+// touch digits below s (the largest m0 + g among them), so each of their tiles
+// lies in one block of b^s consecutive elements and a block's tiles are
+// consecutive in every such pass.  Those passes then run chunk by chunk (a
+// chunk = `per_chunk` blocks, at most the chunk size in elements), so that
+// each pass after the first reads its input from L2; the remaining passes run
+// over the whole data afterwards.  prefix = 0 means no chunking.
+struct ChunkPlan {
+    size_t prefix = 0;
+    long long units = 1, per_chunk = 1;
+};
+
+static ChunkPlan chunk_plan(const gtt_plan_s *P) {
+    ChunkPlan c;
+    long long C = P->chunk_elems;
+    if (C == -1) C = P->total * P->es > (96ll << 20) ? (48ll << 20) / P->es : 0;  // 48 MiB chunks
+    if (C <= 0) return c;
+    int top = 0;
+    long long block = 1;
+    size_t prefix = 0;
+    for (size_t i = 0; i < P->passes.size(); ++i) {
+        top = std::max(top, P->passes[i].m0 + P->passes[i].g);
+        const long long blk = ipow_ll(P->b, top);
+        if (blk > C) break;
+        prefix = i + 1;
+        block = blk;
+    }
+    const long long units = P->total / block, per_chunk = std::max(1ll, C / block);
+    if (prefix < 2 || per_chunk >= units) return c;  // nothing stays in L2 between passes
+    c.prefix = prefix;
+    c.units = units;
+    c.per_chunk = per_chunk;
+    return c;
+}
+
+static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
+                             void *outp, cudaStream_t stream, long long tb, long long te) {
+    if (pp.tc.on) return tc_run(P, pp, &Wb == &P->Wa, in, outp, stream, tb, te);
+    if (pp.tma.on) return tma_run(P, pp, Wb, in, outp, stream, tb, te);
+    PassParams prm = pp.params;
+    prm.tile_begin = tb;
+    prm.tiles = te;
+    const int grid = (int)std::min<long long>(pp.grid, te - tb);
+    void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)Wb.data()};
+    return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
+}
+
 // Launch every pass of the schedule with the given W bytes.
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream) {
-    // With chunking, every pass of a chunk of batch items runs before the next
-    // chunk starts, so the intermediate passes of a chunk read what the
-    // previous pass left in L2.  A batch item's tiles are consecutive in every
-    // pass, so a chunk is a tile range.
-    const long long citems = (P->chunk_items > 0 && P->chunk_items < P->batch) ? P->chunk_items : P->batch;
-    for (long long c0 = 0; c0 < P->batch; c0 += citems) {
-        const long long c1 = std::min(P->batch, c0 + citems);
-        for (size_t i = 0; i < P->passes.size(); ++i) {
+    const ChunkPlan c = chunk_plan(P);
+    for (long long u0 = 0; c.prefix > 0 && u0 < c.units; u0 += c.per_chunk) {
+        const long long u1 = std::min(c.units, u0 + c.per_chunk);
+        for (size_t i = 0; i < c.prefix; ++i) {
             PassPlan &pp = P->passes[i];
-            const long long per_item = pp.params.tiles / P->batch;
-            const long long tb = c0 * per_item, te = c1 * per_item;
-            const void *in = i == 0 ? x : (const void *)y;
-            void *outp = y;
-            gtt_status_t st;
-            if (pp.tc.on) {
-                st = tc_run(P, pp, &Wb == &P->Wa, in, outp, stream, tb, te);
-            } else if (pp.tma.on) {
-                st = tma_run(P, pp, Wb, in, outp, stream, tb, te);
-            } else {
-                PassParams prm = pp.params;
-                prm.tile_begin = tb;
-                prm.tiles = te;
-                const int grid = (int)std::min<long long>(pp.grid, te - tb);
-                void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)Wb.data()};
-                st = launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
-            }
+            const long long per_unit = pp.params.tiles / c.units;
+            gtt_status_t st = run_pass(P, pp, Wb, i == 0 ? x : (const void *)y, y, stream, u0 * per_unit, u1 * per_unit);
             if (st != GTT_OK) return st;
         }
+    }
+    for (size_t i = c.prefix; i < P->passes.size(); ++i) {
+        gtt_status_t st = run_pass(P, P->passes[i], Wb, i == 0 ? x : (const void *)y, y, stream, 0,
+                                   P->passes[i].params.tiles);
+        if (st != GTT_OK) return st;
     }
     return GTT_OK;
 }

@@ -105,7 +105,7 @@ struct gtt_plan_s {
     std::vector<long long> explicit_r;
     int *dev_err = nullptr;              // device flag raised by a bounded wait that expired
     void *d_wpieces = nullptr;           // BF16x3 pieces of W and W^T (b = 16 tensor-core path)
-    long long chunk_items = 0;           // batch items per L2-resident chunk (0: whole batch)
+    long long chunk_elems = 0;           // elements per L2-resident chunk (0: off, -1: automatic)
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
     std::vector<cudaEvent_t> event_pool;

@@ -1,6 +1,7 @@
 """L2-resident chunked execution (gtt_plan_set_chunking): the launch order
 changes, the result does not (bitwise), for the CUDA-core, TMA and
-tensor-core pass kernels."""
+tensor-core pass kernels, with chunks of whole batch items and with chunks of
+blocks inside an item (the leading passes chunked, the rest run after)."""
 import numpy as np
 import pytest
 import torch
@@ -23,9 +24,9 @@ def g():
 @pytest.mark.parametrize("b,n,batch,dt,prec,tma", [
     (16, 4, 7, "f32", "fp32", False), (16, 4, 7, "f32", "fp32", True), (16, 4, 7, "f32", "bf16x3", True),
     (8, 5, 5, "f32", "fp32", True), (4, 7, 6, "c64", "fp32", True), (3, 7, 5, "c64", "fp32", False)])
-@pytest.mark.parametrize("items", [1, 2, 3])
-def test_chunked_passes_are_bitwise_identical(g, b, n, batch, dt, prec, tma, items):
-    rng = np.random.default_rng(9500 + b + items)
+@pytest.mark.parametrize("chunk", ["item1", "item2", "item3", "block", "block3"])
+def test_chunked_passes_are_bitwise_identical(g, b, n, batch, dt, prec, tma, chunk):
+    rng = np.random.default_rng(9500 + b + len(chunk))
     if dt == "c64":
         W = gi.haar_unitary(b, rng).astype(np.complex64)
         x = gi.complex_normal_x((batch, b ** n), rng, np.complex64)
@@ -37,8 +38,18 @@ def test_chunked_passes_are_bitwise_identical(g, b, n, batch, dt, prec, tma, ite
     if prec == "bf16x3":
         plan.set_precision(g.PREC_BF16X3)
     xd = torch.from_numpy(x).cuda()
+    passes = plan.describe()["passes"]
+    if not chunk.startswith("item") and len(passes) < 2:
+        plan.set_passes([n // 2, n - n // 2], [1, 1])  # two passes, so a prefix can be chunked
+        passes = plan.describe()["passes"]
     ref = plan.forward(xd).cpu().numpy()
-    plan.set_chunking(items)
+    if chunk.startswith("item"):
+        elems = int(chunk[4:]) * b ** n
+    else:
+        # blocks of b^s elements, s = the top digit of the first two passes
+        s = max(p["m0"] + p["g"] for p in passes[:2])
+        elems = (3 if chunk == "block3" else 1) * b ** s
+    plan.set_chunking(elems)
     y = plan.forward(xd)
     xr = plan.inverse(y)
     torch.cuda.synchronize()
@@ -53,7 +64,7 @@ def test_chunked_passes_are_bitwise_identical(g, b, n, batch, dt, prec, tma, ite
 def test_automatic_chunking_choice(g):
     W, _ = gi.config_inputs(2)
     plan = g.Plan(W, 6, "f32", 64)
-    plan.set_chunking(-1)   # 64 MiB items, 4 GiB batch: one item per chunk
+    plan.set_chunking(-1)   # 4 GiB: 48 MiB chunks of the first two passes
     small = g.Plan(W, 4, "f32", 2)
     small.set_chunking(-1)  # fits L2 already: stays off
     # (the choice is internal; both must still compute the transform)
