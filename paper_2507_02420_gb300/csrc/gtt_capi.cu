@@ -637,7 +637,7 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                  pp.tc.on ? pp.tc.name.c_str() : t ? pp.tma.name.c_str() : pp.name.c_str(), pp.m0, pp.g,
                  pp.r, pp.D, (long long)pp.params.tile_elems * P->es, pp.params.tiles,
                  pp.tc.on ? pp.tc.grid : t ? pp.tma.grid : pp.grid,
-                 pp.tc.on ? pp.tc.block : t ? kTmaThreads : pp.block,
+                 pp.tc.on ? pp.tc.block : t ? kTmaBlock : pp.block,
                  pp.tc.on ? pp.tc.smem : t ? pp.tma.smem : pp.smem,
                  pp.tc.on ? pp.tc.ctas_per_sm : t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode,
                  t ? "true" : "false", t ? pp.tma.params.nbuf : 0);

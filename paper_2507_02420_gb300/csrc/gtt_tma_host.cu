@@ -100,12 +100,12 @@ bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf) {
     if (t.rows_per_box % 8 != 0 || (!contig && cp.M % 8 != 0)) return false;
     const void *k = tma_kernel((int)P->dtype, b, pp->D, contig);
     if (!k) return false;
-    const size_t smem = (size_t)nbuf * tile_bytes + 1024 + 8 * kTmaMaxBuf;
+    const size_t smem = (size_t)nbuf * tile_bytes + 1024 + kTmaBarBytes;
     if (smem > (size_t)P->smem_optin) return false;
     if (allow_max_smem(k, P->smem_optin) != cudaSuccess) return false;
     if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) return false;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTmaThreads, smem) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTmaBlock, smem) != cudaSuccess || per_sm < 1)
         return false;
     TmaPass &tp = pp->tma;
     tp.params = t;
@@ -170,7 +170,7 @@ gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned cha
     prm.tiles = tile_end;
     const int grid = (int)std::min<long long>(tp.grid, tile_end - tile_begin);
     void *args[4] = {(void *)&tp.map_in, (void *)&tp.map_out, (void *)&prm, (void *)Wb.data()};
-    return launch_timed(P, tp.kern, dim3(grid), dim3(kTmaThreads), args, tp.smem, stream, tp.name);
+    return launch_timed(P, tp.kern, dim3(grid), dim3(kTmaBlock), args, tp.smem, stream, tp.name);
 }
 
 } // namespace gtt
