@@ -214,7 +214,20 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     W, x = gi.config_inputs(1)
+    # plan step: the autotuner times candidate schedules (pass digits, run
+    # lengths, pipeline depth) on this GPU and keeps the fastest; with
+    # --tune-cache an earlier result is reused (a plan applies cached entries
+    # when it is created)
+    cached = bool(args.tune_cache) and os.path.exists(args.tune_cache)
+    if cached and not args.no_autotune:
+        g.autotune_cache_load(args.tune_cache)
     plan = g.Plan(W, NDIG, "c64", BATCH)
+    t_tune = time.perf_counter()
+    if not args.no_autotune and not cached:
+        plan.autotune(400)
+        if args.tune_cache:
+            g.autotune_cache_save(args.tune_cache)
+    t_tune = time.perf_counter() - t_tune
     desc = plan.describe()
     xd = torch.from_numpy(x).to(dev)
     yd = torch.empty_like(xd)
@@ -340,7 +353,9 @@ def run_gpu(args, rank, world, local_rank):
                    "N": N, "step": "one gtt_forward + one gtt_inverse",
                    "l2": "no flush: each 512 MiB operand exceeds the 126 MB L2",
                    "passes_per_transform": len(passes),
-                   "schedule": [[p_["m0"], p_["g"], p_["r"]] for p_ in passes]},
+                   "schedule": [[p_["m0"], p_["g"], p_["r"]] for p_ in passes],
+                   "schedule_source": "default heuristic" if args.no_autotune else
+                   "autotune cache" if cached else f"autotuned at plan time ({t_tune:.1f} s, untimed)"},
         "hbm_gbs_step": alg_bytes_step * args.steps / elapsed_s / 1e9,
         "hbm_frac_step": alg_bytes_step * args.steps / elapsed_s / 1e9 / hbm_peak,
         "inverse_roundtrip_rel_l2": err,
@@ -492,6 +507,10 @@ def main():
     ap.add_argument("--b16-batch", type=int, default=64,
                     help="batch of the b=16 extra (smaller for profiler runs)")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the plan's default schedule instead of the autotuned one")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotune cache file: reused if it exists, else written after tuning")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
