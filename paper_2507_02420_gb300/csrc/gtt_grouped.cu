@@ -15,6 +15,7 @@ struct gtt_group_s {
     int device = 0, count = 0;
     GroupReq *d_reqs = nullptr;
     GroupSeg *d_segs = nullptr;
+    unsigned int *d_item_seg = nullptr;
     unsigned char *d_wblob = nullptr;
     unsigned long long *d_counters = nullptr;  // [0] work counter, then done[nsegs] as uint32
     int *d_err = nullptr;
@@ -37,6 +38,7 @@ gtt_status_t fail(gtt_group_s *G, gtt_status_t st) {
     if (G) {
         if (G->d_reqs) cudaFree(G->d_reqs);
         if (G->d_segs) cudaFree(G->d_segs);
+        if (G->d_item_seg) cudaFree(G->d_item_seg);
         if (G->d_wblob) cudaFree(G->d_wblob);
         if (G->d_counters) cudaFree(G->d_counters);
         if (G->d_err) cudaFree(G->d_err);
@@ -142,16 +144,24 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
             segs.push_back(sg);
         }
 
+    if (items >= (1ll << 31)) return fail(G, set_error(GTT_ERR_UNSUPPORTED, "too many work items in a group"));
+    std::vector<unsigned int> item_seg((size_t)items);
+    for (size_t k = 0; k < segs.size(); ++k)
+        for (long long i = 0; i < segs[k].tiles; ++i) item_seg[(size_t)(segs[k].first_item + i)] = (unsigned int)k;
+
     // device tables
     G->counter_bytes = sizeof(unsigned long long) + segs.size() * sizeof(unsigned int);
     e = cudaMalloc(&G->d_reqs, hreqs.size() * sizeof(GroupReq));
     if (e == cudaSuccess) e = cudaMalloc(&G->d_segs, segs.size() * sizeof(GroupSeg));
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_item_seg, item_seg.size() * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&G->d_wblob, wblob.size());
     if (e == cudaSuccess) e = cudaMalloc(&G->d_counters, G->counter_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&G->d_err, sizeof(int));
     if (e != cudaSuccess) return fail(G, set_error(GTT_ERR_ALLOC, "group device tables"));
     e = cudaMemcpy(G->d_reqs, hreqs.data(), hreqs.size() * sizeof(GroupReq), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_segs, segs.data(), segs.size() * sizeof(GroupSeg), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(G->d_item_seg, item_seg.data(), item_seg.size() * sizeof(unsigned int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_wblob, wblob.data(), wblob.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(G->d_err, 0, sizeof(int));
     if (e != cudaSuccess) return fail(G, cuda_error(e, "group table upload"));
@@ -159,6 +169,7 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
     GroupArgs &a = G->args;
     a.reqs = G->d_reqs;
     a.segs = G->d_segs;
+    a.item_seg = G->d_item_seg;
     a.nsegs = (int)segs.size();
     a.total_items = items;
     a.wblob = G->d_wblob;

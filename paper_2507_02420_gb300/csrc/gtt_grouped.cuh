@@ -3,25 +3,31 @@
 //
 // The work list is a sequence of segments; a segment is one pass of one
 // request, split into tiles (the tile geometry of gtt_pass_kernel).  CTAs take
-// work items (segment, tile) from a global atomic counter in list order.  A
+// work items (segment, tile) from a global atomic counter in list order (a
+// table maps every item to its segment); a CTA fetches its next item's index
+// while it works on the current one, and waits for that item's dependency only
+// after the current item is complete.  A
 // segment of pass p > 0 may only start once every tile of pass p-1 of the same
 // request is done; the host orders the list so that pass p of request q comes
 // `lag` requests after pass p-1 of q, so the wait is normally already
-// satisfied and the previous pass's output is still in L2.  Because items are
-// taken in order and a CTA finishes its item before taking the next, every
-// awaited item has been taken by a running CTA, so the waits always end; each
-// is still bounded (kGroupSpinLimit polls) and an expiry raises the error flag.
+// satisfied and the previous pass's output is still in L2.  The waits always
+// end: items are taken in list order, so every awaited item has been taken by
+// a running CTA, which either works on it (an item in work waits for nothing)
+// or holds it as its next item and reaches it after finishing its current one;
+// a wait only ever points to earlier items, so no cycle forms.  Each wait is
+// still bounded (kGroupSpinLimit polls) and an expiry raises the error flag.
 //
 // W of every request lives in a device blob (the kernels' parameter layout);
-// each item copies its W into shared memory.  Tile data is read with
-// L2-coherent loads (ld.global.cg): an earlier pass on another SM wrote it.
+// an item copies its W into shared memory unless the previous item of the CTA
+// had the same W.  Tile data is read with L2-coherent loads (ld.global.cg, 16
+// bytes wide where the tile rows allow): an earlier pass on another SM wrote it.
 #pragma once
 #include "gtt_internal.h"
 
 namespace gtt {
 
 constexpr int kGroupMaxPass = 6;
-constexpr int kGroupThreads = 256;
+constexpr int kGroupThreads = 128;
 constexpr uint32_t kGroupSpinLimit = 1u << 26;
 
 struct GroupPass {
@@ -45,6 +51,7 @@ struct GroupSeg {
 struct GroupArgs {
     const GroupReq *reqs;
     const GroupSeg *segs;
+    const unsigned int *item_seg;      // segment of every work item
     int nsegs;
     long long total_items;
     const unsigned char *wblob;
@@ -69,14 +76,28 @@ template <typename T, int B, int D>
 __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p, long long t, T *s,
                                         const WMat<T, B> &W) {
     constexpr int RB = cpow(B, D);
+    constexpr int CE = Vec16<T>::n;
     const uint32_t tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tile_elems = p.tile_elems, r = p.r;
     const long long hi = t / p.lo_blocks;
     const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
     const long long base = hi * p.L * (long long)p.M + (long long)lob * r;
-    for (uint32_t e = tid; e < tile_elems; e += nth) {
-        const uint32_t row = p.div_r.div(e), col = e - row * r;
-        s[spos<RB>(e)] = ld_cg(in + base + (long long)row * p.L + col);
+    if (p.vec_mode != 0) {  // 16-byte chunks: contiguous tile (1) or rows of r, r % CE == 0 (2)
+        const uint32_t cpr = p.vec_mode == 1 ? tile_elems / CE : r / CE;
+        const long long rstride = p.vec_mode == 1 ? 0 : p.L;
+        for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
+            const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
+            const int4 raw = __ldcg(reinterpret_cast<const int4 *>(in + base + (long long)row * rstride + cc * CE));
+            const T *v = reinterpret_cast<const T *>(&raw);
+            const uint32_t e0 = p.vec_mode == 1 ? c * CE : row * r + cc * CE;
+#pragma unroll
+            for (int i = 0; i < CE; ++i) s[spos<RB>(e0 + i)] = v[i];
+        }
+    } else {
+        for (uint32_t e = tid; e < tile_elems; e += nth) {
+            const uint32_t row = p.div_r.div(e), col = e - row * r;
+            s[spos<RB>(e)] = ld_cg(in + base + (long long)row * p.L + col);
+        }
     }
     __syncthreads();
     const uint32_t nslots = tile_elems / RB;
@@ -98,9 +119,22 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
         }
         __syncthreads();
     }
-    for (uint32_t e = tid; e < tile_elems; e += nth) {
-        const uint32_t row = p.div_r.div(e), col = e - row * r;
-        out[base + (long long)row * p.L + col] = s[spos<RB>(e)];
+    if (p.vec_mode != 0) {
+        const uint32_t cpr = p.vec_mode == 1 ? tile_elems / CE : r / CE;
+        const long long rstride = p.vec_mode == 1 ? 0 : p.L;
+        for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
+            const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
+            const uint32_t e0 = p.vec_mode == 1 ? c * CE : row * r + cc * CE;
+            T v[CE];
+#pragma unroll
+            for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(e0 + i)];
+            store16(out + base + (long long)row * rstride + cc * CE, v);
+        }
+    } else {
+        for (uint32_t e = tid; e < tile_elems; e += nth) {
+            const uint32_t row = p.div_r.div(e), col = e - row * r;
+            out[base + (long long)row * p.L + col] = s[spos<RB>(e)];
+        }
     }
 }
 
@@ -134,25 +168,26 @@ __device__ __forceinline__ void group_dispatch(const GroupReq &rq, const GroupPa
     }
 }
 
-__global__ void __launch_bounds__(kGroupThreads, 2) gtt_grouped_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(kGroupThreads, 4) gtt_grouped_kernel(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
-    __shared__ int s_seg;
+    __shared__ int s_seg, s_woff;
     const uint32_t tid = threadIdx.x;
+    long long next = 0;  // thread 0: the item taken ahead of the current one
+    if (tid == 0) {
+        next = (long long)atomicAdd(a.work_counter, 1ull);
+        s_woff = -1;
+    }
     for (;;) {
         if (tid == 0) {
-            const long long item = (long long)atomicAdd(a.work_counter, 1ull);
-            int lo = 0, hi = a.nsegs - 1, seg = 0;
-            if (item < a.total_items) {  // last segment whose first_item <= item
-                while (lo <= hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (a.segs[mid].first_item <= item) {
-                        seg = mid;
-                        lo = mid + 1;
-                    } else {
-                        hi = mid - 1;
-                    }
-                }
+            const long long item = next;
+            int seg = 0;
+            if (item < a.total_items) {
+                // take the next item now; its dependency is waited for only
+                // after this item is complete, so a CTA never blocks while it
+                // holds an unfinished item
+                next = (long long)atomicAdd(a.work_counter, 1ull);
+                seg = (int)a.item_seg[item];
                 const int dep = a.segs[seg].dep;
                 if (dep >= 0) {  // bounded wait for the previous pass of this request
                     const unsigned int need = (unsigned int)a.segs[dep].tiles;
@@ -176,14 +211,16 @@ __global__ void __launch_bounds__(kGroupThreads, 2) gtt_grouped_kernel(GroupArgs
         const GroupSeg &sg = a.segs[s_seg];
         const GroupReq &rq = a.reqs[sg.req];
         const GroupPass &gp = rq.pass[sg.pass];
-        // W of this request into shared memory
-        {
+        // W of this request into shared memory, unless it is already there
+        const bool new_w = rq.w_off != s_woff;
+        if (new_w) {
             const int wb = a.w_smem_bytes;
             const int4 *src = reinterpret_cast<const int4 *>(a.wblob + rq.w_off);
             int4 *dst = reinterpret_cast<int4 *>(smem);
             for (int i = tid; i < wb / 16; i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
+        if (tid == 0 && new_w) s_woff = rq.w_off;  // read again only after the next barrier
         const long long t = item - sg.first_item;
         if (rq.dtype == 1)
             group_dispatch<float>(rq, gp, t, smem, a.w_smem_bytes, sg.pass == 0);
