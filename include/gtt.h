@@ -116,8 +116,10 @@ gtt_status_t gtt_plan_set_schedule(gtt_plan_t plan, long long max_tile_bytes,
  * gtt_plan_set_passes -- set the fusion schedule explicitly.  Pass k applies
  * digits[k] consecutive modes (the first pass starts at digit 0, each next
  * pass where the previous one ended; the digits must sum to n) to tiles of
- * b^digits[k] rows of runs[k] contiguous elements.  runs[0] must be 1; for
- * k > 0, runs[k] must divide b^(digits before pass k).  A tile (rows x run)
+ * b^digits[k] rows of runs[k] contiguous elements.  For k > 0, runs[k] must
+ * divide b^(digits before pass k).  The first pass has no lower digits:
+ * runs[0] = k means tiles of k consecutive blocks of b^digits[0] contiguous
+ * elements (k must divide batch * b^(n - digits[0])).  A tile (rows x run)
  * must fit 220 KiB.  Errors: GTT_ERR_INVALID_ARG (bad counts, sums, runs or
  * sizes), GTT_ERR_UNSUPPORTED, GTT_ERR_CUDA.
  */

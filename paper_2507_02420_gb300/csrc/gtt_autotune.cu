@@ -131,8 +131,9 @@ static void enumerate(const gtt_plan_s *P, int m0, std::vector<int> &g, std::vec
     long long L = 1;
     for (int i = 0; i < m0; ++i) L *= b;
     std::vector<long long> runs;
-    if (m0 == 0) {
-        runs.push_back(1);
+    if (m0 == 0) {  // blocks per contiguous tile: 1, 2, 4, 8
+        for (long long k = 1; k <= 8; k *= 2)
+            if (P->total % k == 0) runs.push_back(k);
     } else {
         long long rr = 1;
         bool have32 = false, have128 = false;
@@ -158,6 +159,7 @@ static void enumerate(const gtt_plan_s *P, int m0, std::vector<int> &g, std::vec
         for (long long rr : runs) {
             const long long bytes = M * rr * es;
             if (bytes > 200 * 1024) continue;
+            if (m0 == 0 && P->total % (M * rr) != 0) continue;
             if (bytes < 2048 && gg < remaining && M * rr < (long long)P->total) continue;
             g.push_back(gg);
             r.push_back(rr);

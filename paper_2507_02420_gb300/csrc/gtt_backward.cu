@@ -5,11 +5,17 @@
 // recomputed activations of its digits fit shared memory.  Pass j needs the
 // activation a^(j) entering it and the gradient leaving it:
 //   - a^(0) = x; a^(j), j >= 1, is recomputed by running forward passes
-//     0..j-1 of the same schedule into a checkpoint buffer;
+//     0..j-1 of the same schedule (on the TMA pass kernel where the geometry
+//     allows it);
 //   - the gradient buffer is dx (or a plan-owned buffer when dx is NULL); the
 //     last pass reads dy, every pass writes its input gradient in place.
-// With two passes and dx distinct from dy, dx itself holds the checkpoint
-// a^(1) until the last pass overwrites it with the gradient.
+// Checkpoints: with two passes, a^(1) is computed once into dx (when dx is
+// distinct from dy) or a plan-owned buffer.  With three passes and a gradient
+// buffer distinct from dy, a^(1) goes to the checkpoint buffer and a^(2) to
+// the gradient buffer, which the first backward pass reads as its activation
+// and overwrites, tile by tile, with its gradient (a tile is read whole before
+// it is written).  Otherwise a^(j) is recomputed into the checkpoint buffer
+// before each pass.
 // dW partials (one b x b block per CTA and pass) are summed in a fixed order.
 #include <algorithm>
 #include <cstring>
@@ -64,6 +70,7 @@ gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
         if (st != GTT_OK) return st;
         st = build_pass(P, m0, g, r, g >= DM ? DM : 1, &bp.fwd);  // forward recompute of a^(j+1)
         if (st != GTT_OK) return st;
+        if (P->use_tma) tma_attach(P, &bp.fwd, P->tma_nbuf);  // stays on the CUDA-core kernel if ineligible
         bp.kern = bk;
         bp.smem = bwd_smem_bytes(b, g, ipow_ll(b, g) * r, es, cplx);
         if (bp.smem > 227 * 1024) return set_error(GTT_ERR_UNSUPPORTED, "backward tile exceeds shared memory");
@@ -132,6 +139,7 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
     }
     // checkpoint buffer
     void *CK = nullptr;
+    const bool two_ck = m == 3 && GB != dy;  // a^(2) parked in the gradient buffer
     if (m >= 2) {
         if (m == 2 && dx && dx != dy) {
             CK = dx;
@@ -148,18 +156,33 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
     if (st != GTT_OK) return st;
 
     const std::vector<unsigned char> &Wf = P->Wf, &Wa = P->Wa;
+    auto fwd_pass = [&](int q, const void *in, void *outp) -> gtt_status_t {
+        PassPlan &fp = P->bwd[q].fwd;
+        if (fp.tma.on) return tma_run(P, fp, Wf, in, outp, s, 0, fp.params.tiles);
+        void *args[4] = {(void *)&in, (void *)&outp, (void *)&fp.params, (void *)Wf.data()};
+        return launch_timed(P, fp.kern, dim3(fp.grid), dim3(fp.block), args, fp.smem, s, fp.name);
+    };
+    // activations entering each backward pass, computed up front when they fit
+    std::vector<const void *> act(m, x);
+    bool upfront = false;
+    if (m == 2 || two_ck) {
+        st = fwd_pass(0, x, CK);
+        if (st != GTT_OK) return st;
+        act[1] = CK;
+        if (two_ck) {
+            st = fwd_pass(1, CK, GB);
+            if (st != GTT_OK) return st;
+            act[2] = GB;
+        }
+        upfront = true;
+    }
     size_t part_off = 0;
     for (int j = m - 1; j >= 0; --j) {
         const BwdPass &bp = P->bwd[j];
-        // a^(j): x for the first pass, else forward passes 0..j-1 into CK
-        const void *A = x;
-        if (j >= 1) {
+        const void *A = act[j];
+        if (!upfront && j >= 1) {  // a^(j): forward passes 0..j-1 into CK
             for (int q = 0; q < j; ++q) {
-                const PassPlan &fp = P->bwd[q].fwd;
-                const void *in = q == 0 ? x : (const void *)CK;
-                void *outp = CK;
-                void *args[4] = {(void *)&in, (void *)&outp, (void *)&fp.params, (void *)Wf.data()};
-                st = launch_timed(P, fp.kern, dim3(fp.grid), dim3(fp.block), args, fp.smem, s, fp.name);
+                st = fwd_pass(q, q == 0 ? x : (const void *)CK, CK);
                 if (st != GTT_OK) return st;
             }
             A = CK;
@@ -179,7 +202,7 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
         const void *parts = P->ws_dw;
         int bb = P->b * P->b;
         void *args[4] = {(void *)&parts, (void *)&nparts, (void *)&bb, (void *)&dW};
-        st = launch_timed(P, rk, dim3((bb + 255) / 256), dim3(256), args, 0, s, "gtt_dw_reduce_kernel");
+        st = launch_timed(P, rk, dim3((bb + kDwEntriesPerBlock - 1) / kDwEntriesPerBlock), dim3(32 * kDwEntriesPerBlock), args, 0, s, "gtt_dw_reduce_kernel");
         if (st != GTT_OK) return st;
     }
     return GTT_OK;

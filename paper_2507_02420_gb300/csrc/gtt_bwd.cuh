@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kBwdThreads)
 gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_part, PassParams p,
                          int g, WMat<T, B> W, WMat<T, B> WH) {
     constexpr int GS = B / R;  // threads per fibre group
+    constexpr int CE = Vec16<T>::n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
     const uint32_t tile = p.tile_elems, r = p.r;
@@ -72,11 +73,29 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
         const long long hi = t / p.lo_blocks;
         const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
         const long long base = hi * LM + (long long)lob * r;
-        for (uint32_t e = tid; e < tile; e += nth) {
-            const uint32_t row = p.div_r.div(e), col = e - row * r;
-            const long long ga = base + (long long)row * p.L + col;
-            s[spos<B>(e)] = act_in[ga];
-            G[spos<B>(e)] = grad_out[ga];
+        if (p.vec_mode != 0) {  // 16-byte chunks: contiguous tile (1) or rows of r, r % CE == 0 (2)
+            const uint32_t cpr = p.vec_mode == 1 ? tile / CE : r / CE;
+            const long long rstride = p.vec_mode == 1 ? 0 : p.L;
+            for (uint32_t c = tid; c < tile / CE; c += nth) {
+                const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
+                const long long ga = base + (long long)row * rstride + cc * CE;
+                T va[CE], vg[CE];
+                load16(act_in + ga, va);
+                load16(grad_out + ga, vg);
+                const uint32_t e0 = p.vec_mode == 1 ? c * CE : row * r + cc * CE;
+#pragma unroll
+                for (int i = 0; i < CE; ++i) {
+                    s[spos<B>(e0 + i)] = va[i];
+                    G[spos<B>(e0 + i)] = vg[i];
+                }
+            }
+        } else {
+            for (uint32_t e = tid; e < tile; e += nth) {
+                const uint32_t row = p.div_r.div(e), col = e - row * r;
+                const long long ga = base + (long long)row * p.L + col;
+                s[spos<B>(e)] = act_in[ga];
+                G[spos<B>(e)] = grad_out[ga];
+            }
         }
         __syncthreads();
 
@@ -137,9 +156,22 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
             __syncthreads();
         }
 
-        for (uint32_t e = tid; e < tile; e += nth) {
-            const uint32_t row = p.div_r.div(e), col = e - row * r;
-            grad_in[base + (long long)row * p.L + col] = G[spos<B>(e)];
+        if (p.vec_mode != 0) {
+            const uint32_t cpr = p.vec_mode == 1 ? tile / CE : r / CE;
+            const long long rstride = p.vec_mode == 1 ? 0 : p.L;
+            for (uint32_t c = tid; c < tile / CE; c += nth) {
+                const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
+                const uint32_t e0 = p.vec_mode == 1 ? c * CE : row * r + cc * CE;
+                T v[CE];
+#pragma unroll
+                for (int i = 0; i < CE; ++i) v[i] = G[spos<B>(e0 + i)];
+                store16(grad_in + base + (long long)row * rstride + cc * CE, v);
+            }
+        } else {
+            for (uint32_t e = tid; e < tile; e += nth) {
+                const uint32_t row = p.div_r.div(e), col = e - row * r;
+                grad_in[base + (long long)row * p.L + col] = G[spos<B>(e)];
+            }
         }
         __syncthreads();
     }
@@ -159,25 +191,40 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
     }
 }
 
-// dW[e] = sum over parts (in order) of part[q][e], accumulated in double.
+// dW[e] = sum over parts of part[q][e], accumulated in double: one warp per
+// entry, lane l adds parts l, l+32, l+64, ... in order, then a fixed butterfly
+// combines the lanes, so the result is the same on every run.
+constexpr int kDwEntriesPerBlock = 8;  // warps of a 256-thread block
+
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <typename T>
-__global__ void gtt_dw_reduce_kernel(const T *parts, int nparts, int bb, T *dW) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= bb) return;
+__global__ void __launch_bounds__(32 * kDwEntriesPerBlock) gtt_dw_reduce_kernel(const T *parts, int nparts, int bb, T *dW) {
+    const int e = blockIdx.x * kDwEntriesPerBlock + (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    if (e >= bb) return;  // whole warps leave together
     if constexpr (Traits<T>::complex) {
         double re = 0.0, im = 0.0;
-        for (int q = 0; q < nparts; ++q) {
+        for (int q = lane; q < nparts; q += 32) {
             re += (double)parts[(size_t)q * bb + e].re;
             im += (double)parts[(size_t)q * bb + e].im;
         }
-        T out;
-        out.re = (typename Traits<T>::real)re;
-        out.im = (typename Traits<T>::real)im;
-        dW[e] = out;
+        re = warp_sum_fixed(re);
+        im = warp_sum_fixed(im);
+        if (lane == 0) {
+            T out;
+            out.re = (typename Traits<T>::real)re;
+            out.im = (typename Traits<T>::real)im;
+            dW[e] = out;
+        }
     } else {
         double acc = 0.0;
-        for (int q = 0; q < nparts; ++q) acc += (double)parts[(size_t)q * bb + e];
-        dW[e] = (T)acc;
+        for (int q = lane; q < nparts; q += 32) acc += (double)parts[(size_t)q * bb + e];
+        acc = warp_sum_fixed(acc);
+        if (lane == 0) dW[e] = (T)acc;
     }
 }
 

@@ -36,6 +36,9 @@ static long long ipow_ll(int b, int e) {
 }
 
 // Build the launch description of one pass (modes [m0, m0+g), run r, window D).
+// The first pass has no lower digits to run over; there r > 1 means tiles of r
+// consecutive blocks of b^g contiguous elements (the register stages treat the
+// block index like any digit above their window, and leave it untouched).
 gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPlan *out) {
     const int b = P->b, es = P->es;
     PassPlan pp;
@@ -43,8 +46,14 @@ gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPl
     pp.g = g;
     pp.D = D;
     pp.r = r;
-    const long long L = ipow_ll(b, m0), M = ipow_ll(b, g);
+    long long kblk = 1;
+    if (m0 == 0 && r > 1) {
+        kblk = r;
+        r = 1;
+    }
+    const long long L = ipow_ll(b, m0), M = ipow_ll(b, g) * kblk;
     if (L % r != 0 || g < D || g < 1) return set_error(GTT_ERR_INTERNAL, "bad pass geometry");
+    if (P->total % (M * r) != 0) return set_error(GTT_ERR_INVALID_ARG, "blocks per tile must divide the data");
     if (L / r > (1ll << 31) || M * r > (1ll << 24))
         return set_error(GTT_ERR_UNSUPPORTED, "pass geometry exceeds 32-bit tile indexing");
     const long long tile = M * r;
@@ -316,7 +325,7 @@ gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits,
         long long L = 1, M = 1;
         for (int i = 0; i < m0; ++i) L *= b;
         for (int i = 0; i < g; ++i) M *= b;
-        if (r < 1 || L % r != 0 || (k == 0 && r != 1)) return set_error(GTT_ERR_INVALID_ARG, "run must divide b^m0");
+        if (r < 1 || (k > 0 && L % r != 0)) return set_error(GTT_ERR_INVALID_ARG, "run must divide b^m0");
         if (M * r * es > 220 * 1024) return set_error(GTT_ERR_INVALID_ARG, "tile above 220 KiB");
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, g >= DM ? DM : 1, &pp);
@@ -349,6 +358,7 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     const int old_nbuf = P->tma_nbuf;
     P->use_tma = use_tma != 0;
     P->tma_nbuf = nbuf;
+    P->bwd_ready = false;  // the backward's recompute passes follow the pipeline choice
     std::vector<PassPlan> passes;
     gtt_status_t st = P->explicit_g.empty()
                           ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
@@ -481,6 +491,8 @@ static ChunkPlan chunk_plan(const gtt_plan_s *P) {
         top = std::max(top, P->passes[i].m0 + P->passes[i].g);
         const long long blk = ipow_ll(P->b, top);
         if (blk > C) break;
+        // a first-pass tile of several blocks must not straddle a chunk block
+        if (P->passes[i].m0 == 0 && blk % P->passes[i].params.tile_elems != 0) break;
         prefix = i + 1;
         block = blk;
     }

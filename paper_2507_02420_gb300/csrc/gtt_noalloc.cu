@@ -116,7 +116,7 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
         const void *parts = scratch;
         int bb = P->b * P->b;
         void *args[4] = {(void *)&parts, (void *)&nparts, (void *)&bb, (void *)&dW};
-        e = cudaLaunchKernel(rk, dim3((bb + 255) / 256), dim3(256), args, 0, s);
+        e = cudaLaunchKernel(rk, dim3((bb + kDwEntriesPerBlock - 1) / kDwEntriesPerBlock), dim3(32 * kDwEntriesPerBlock), args, 0, s);
         if (e != cudaSuccess) return cuda_error(e, "dW reduction launch");
     }
     return GTT_OK;

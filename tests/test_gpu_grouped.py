@@ -151,13 +151,15 @@ def test_explicit_schedule_and_rejections(g):
     x = gi.normal_x((2, 8 ** 6), rng, np.float32)
     plan = g.Plan(W, 6, "f32", 2)
     ref = oracle.modes(up(W), up(x))
+    # (a first-pass run k > 1 means tiles of k consecutive blocks of 8^digits[0])
     for digits, runs in (([3, 3], [1, 64]), ([2, 2, 2], [1, 8, 64]), ([5, 1], [1, 8]),
-                         ([1] * 6, [1, 8, 8, 8, 8, 8])):
+                         ([1] * 6, [1, 8, 8, 8, 8, 8]), ([3, 3], [2, 64]), ([2, 4], [8, 8])):
         plan.set_passes(digits, runs)
         y = plan.forward(torch.from_numpy(x).cuda())
         torch.cuda.synchronize()
         assert rel(y.cpu().numpy(), ref) <= 2e-6, digits
-    # digits not summing to n, a first run != 1, a run not dividing b^m0, a 1 MiB tile
-    for digits, runs in (([3, 2], [1, 8]), ([3, 3], [2, 8]), ([3, 3], [1, 7]), ([6], [1])):
+    # digits not summing to n, first-pass blocks not dividing the data, a run
+    # not dividing b^m0, a 1 MiB tile
+    for digits, runs in (([3, 2], [1, 8]), ([3, 3], [3, 8]), ([3, 3], [1, 7]), ([6], [1])):
         with pytest.raises(g.GTTError):
             plan.set_passes(digits, runs)
