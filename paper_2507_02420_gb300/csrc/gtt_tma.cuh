@@ -43,6 +43,8 @@ __host__ __device__ constexpr int tma_min_blocks(int es, int B, int D) {
     return (B <= 8 && cpow(B, D) <= 16 && cpow(B, D) * es <= 128) ? 3 : 1;
 }
 
+constexpr int kTmaXorStages = 8;  // stages that can use the table-driven address form
+
 struct TmaParams {
     long long tiles;          // end of this launch's tile range
     long long tile_begin;     // first tile of this launch's range
@@ -59,6 +61,7 @@ struct TmaParams {
     FastDiv stage_divBa[kMaxStages];
     int stage_addr[kMaxStages];       // address form of the stage (kAddr*)
     uint32_t stage_stride[kMaxStages];  // bytes between register elements (kAddrStride)
+    uint32_t stage_fq[kTmaXorStages][16];  // swizzled offset of register element q (kAddrXor)
     int *err;  // device flag: 1 = an mbarrier wait expired
 };
 
@@ -68,8 +71,13 @@ struct TmaParams {
 //   kAddrStride   the swizzle phase (row mod 8) and the byte in the row are the
 //                 same for every element: a fixed byte stride;
 //   kAddrRowXor   element q sits q rows after a row that is a multiple of 8, at
-//                 the same byte: the 16-byte chunk index is XORed with q mod 8.
-constexpr int kAddrGeneral = 0, kAddrStride = 1, kAddrRowXor = 2;
+//                 the same byte: the 16-byte chunk index is XORed with q mod 8;
+//   kAddrXor      any power-of-two geometry: the byte offset of a tile element
+//                 is a GF(2)-linear function F of its index bits (bit moves and
+//                 the 128B-swizzle XOR), and the window base and q * Ba occupy
+//                 disjoint bits, so offset(q) = F(base) ^ F(q * Ba), with the
+//                 second term tabulated per stage on the host (stage_fq).
+constexpr int kAddrGeneral = 0, kAddrStride = 1, kAddrRowXor = 2, kAddrXor = 3;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -305,7 +313,15 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
                         }
                     }
                     const int form = p.stage_addr[st];
-                    if (form == kAddrStride) {
+                    if (form == kAddrXor) {
+                        const uint32_t a0 = Tile::off(row0, col, p.M);
+                        const uint32_t *fq = p.stage_fq[st];
+#pragma unroll
+                        for (int q = 0; q < RB; ++q) v[q] = *reinterpret_cast<const T *>(tb + (a0 ^ fq[q]));
+                        apply_window<T, B, D>(v, mask, W);
+#pragma unroll
+                        for (int q = 0; q < RB; ++q) *reinterpret_cast<T *>(tb + (a0 ^ fq[q])) = v[q];
+                    } else if (form == kAddrStride) {
                         unsigned char *a0 = tb + Tile::off(row0, col, p.M);
                         const uint32_t stride = p.stage_stride[st];
 #pragma unroll

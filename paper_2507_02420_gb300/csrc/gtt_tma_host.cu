@@ -27,6 +27,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 static bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Host copy of the kernel's tile offset (TmaTile::off): byte offset of tile
+// element (row, col) in the 128B-swizzled buffer.
+static uint32_t host_swz(uint32_t s, uint32_t ccb) { return (s << 7) + ((((ccb >> 4) ^ s) & 7u) << 4) + (ccb & 15u); }
+static uint32_t host_tile_off(bool contig, uint32_t es, uint32_t row, uint32_t col, uint32_t M) {
+    const uint32_t R128 = 128 / es;
+    return contig ? host_swz(row / R128, (row % R128) * es) : host_swz((col / R128) * M + row, (col % R128) * es);
+}
+
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf) {
     pp->tma = TmaPass();
     const int b = P->b, es = P->es;
@@ -62,6 +70,11 @@ bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf) {
         // address form (see kAddr* in gtt_tma.cuh); M % 8 == 0 is required below
         t.stage_addr[s] = kAddrGeneral;
         t.stage_stride[s] = 0;
+        if (s < kTmaXorStages && RB <= 16) {  // b and hence Ba, M, R128 are powers of two
+            t.stage_addr[s] = kAddrXor;
+            for (long long q = 0; q < RB; ++q)
+                t.stage_fq[s][q] = host_tile_off(contig_tile, (uint32_t)es, (uint32_t)(q * Ba), 0, cp.M);
+        }
         if (!contig_tile) {
             if (Ba % 8 == 0) {
                 t.stage_addr[s] = kAddrStride;
