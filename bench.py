@@ -116,7 +116,7 @@ def gpu_smi_id(dev_index: int) -> str:
 
 
 # --------------------------------------------------------- oracle baseline
-def oracle_pairs_gelems(W, x, min_seconds: float, max_reps: int = 8):
+def oracle_pairs_gelems(W, x, min_seconds: float, max_reps: int = 64):
     """Time the FP64 oracle (forward + inverse pairs) on the host cores."""
     import oracle
     threads = os.cpu_count() or 1

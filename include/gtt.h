@@ -243,6 +243,19 @@ gtt_status_t gtt_inverse_host(gtt_plan_t plan, const void *y_host, void *x_host,
                               gtt_stream_t stream);
 
 /*
+ * gtt_selftest_bounded_wait -- check, on the current device and without any
+ * fault, that the bounded waits of the library's pipelined kernels give up:
+ * one warp waits on an mbarrier that nothing arrives on, using the kernels'
+ * try-wait primitive, for at most `polls` polls (1 .. 2^20), and reports the
+ * expiry through a device flag, as the pass kernels do before
+ * gtt_plan_check returns GTT_ERR_TIMEOUT.  *expired = 1 when the wait expired
+ * (the expected outcome).  Synchronizes `stream`.  No counterpart in the paper.
+ * Errors: GTT_ERR_INVALID_ARG (polls out of range, NULL expired),
+ * GTT_ERR_ALLOC, GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_selftest_bounded_wait(int polls, int *expired, gtt_stream_t stream);
+
+/*
  * gtt_plan_describe -- write a one-line JSON description of the plan's
  * schedule (passes, digits per pass, run length, tile bytes, kernels
  * launched per transform) into buf (NUL-terminated, truncated to len).

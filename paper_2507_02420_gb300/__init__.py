@@ -9,5 +9,5 @@ from .api import (C64, C128, F32, F64, I32, PREC_AUTO, PREC_BF16X3, PREC_FP32, P
                   dtype_code)
 from ._lib import GTTError, LIB_PATH, load  # noqa: F401
 from .autograd import GTTFunction, gtt  # noqa: F401
-from .api import autotune_cache_load, autotune_cache_save  # noqa: F401
+from .api import autotune_cache_load, autotune_cache_save, selftest_bounded_wait  # noqa: F401
 from .group import Group  # noqa: F401

@@ -46,6 +46,7 @@ SIGNATURES = {
     "gtt_group_check": (_I, [_P]),
     "gtt_group_describe": (_I, [_P, ctypes.c_char_p, _S]),
     "gtt_group_destroy": (_I, [_P]),
+    "gtt_selftest_bounded_wait": (_I, [_I, ctypes.POINTER(_I), _P]),
 }
 
 _lock = threading.Lock()

@@ -206,3 +206,12 @@ def autotune_cache_load(path: str):
 
 def autotune_cache_save(path: str):
     check(load().gtt_autotune_cache_save(path.encode()), "gtt_autotune_cache_save")
+
+
+def selftest_bounded_wait(polls: int = 1000, stream=None) -> bool:
+    """Run gtt_selftest_bounded_wait: True when the bounded mbarrier wait
+    expired (the expected outcome), reported through a device flag."""
+    out = ctypes.c_int(0)
+    check(load().gtt_selftest_bounded_wait(int(polls), ctypes.byref(out), _stream_ptr(stream)),
+          "gtt_selftest_bounded_wait")
+    return bool(out.value)
