@@ -16,6 +16,8 @@
 // partial per CTA; gtt_dw_reduce_kernel adds the partials of all CTAs and
 // passes in a fixed order, so dW is bitwise reproducible.
 #pragma once
+#include <type_traits>
+
 #include "gtt_pass.cuh"
 
 namespace gtt {
@@ -99,22 +101,35 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
         }
         __syncthreads();
 
+        // Window element q of a fibre sits at spos(e0 + q * strideA).  That is
+        // linear in q when strideA is a multiple of B, or 1 with e0 a multiple
+        // of B (always the case for power-of-b runs): spos(e0) + q * step.
         // forward recompute: A_{k+1} = mode k applied to A_k, k = 0 .. g-2
         for (int k = 0; k + 1 < g; ++k) {
             const T *A = s + (size_t)k * tstride;
             T *An = s + (size_t)(k + 1) * tstride;
             const uint32_t strideA = p.stage_strideA[k];
+            const bool lin = strideA == 1u || strideA % B == 0u;
+            const uint32_t step = strideA == 1u ? 1u : strideA + strideA / B;
             for (uint32_t f = tid; f < nfib; f += nth) {
                 const uint32_t rest = p.div_r.div(f), col = f - rest * r;
                 const uint32_t high = p.stage_divBa[k].div(rest);
                 const uint32_t low = rest - high * p.stage_divBa[k].d;
                 const uint32_t e0 = high * (strideA * B) + low * r + col;
-                T v[B];
+                auto body = [&](auto pos) {
+                    T v[B];
 #pragma unroll
-                for (int q = 0; q < B; ++q) v[q] = A[spos<B>(e0 + q * strideA)];
-                apply_window<T, B, 1>(v, 1, W);
+                    for (int q = 0; q < B; ++q) v[q] = A[pos(q)];
+                    apply_window<T, B, 1>(v, 1, W);
 #pragma unroll
-                for (int q = 0; q < B; ++q) An[spos<B>(e0 + q * strideA)] = v[q];
+                    for (int q = 0; q < B; ++q) An[pos(q)] = v[q];
+                };
+                if (lin) {
+                    const uint32_t sb = spos<B>(e0);
+                    body([&](int q) { return sb + (uint32_t)q * step; });
+                } else {
+                    body([&](int q) { return spos<B>(e0 + (uint32_t)q * strideA); });
+                }
             }
             __syncthreads();
         }
@@ -123,35 +138,69 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
         for (int k = g - 1; k >= 0; --k) {
             const T *A = s + (size_t)k * tstride;
             const uint32_t strideA = p.stage_strideA[k];
+            const bool lin = strideA == 1u || strideA % B == 0u;
+            const uint32_t step = strideA == 1u ? 1u : strideA + strideA / B;
             for (uint32_t slot = tid; slot < nfib * GS; slot += nth) {
                 const uint32_t f = slot / GS, ib = slot % GS;
                 const uint32_t rest = p.div_r.div(f), col = f - rest * r;
                 const uint32_t high = p.stage_divBa[k].div(rest);
                 const uint32_t low = rest - high * p.stage_divBa[k].d;
                 const uint32_t e0 = high * (strideA * B) + low * r + col;
-                T a[B], gv[B];
+                auto body = [&](auto pos) {
+                    T a[B], gv[B];
 #pragma unroll
-                for (int q = 0; q < B; ++q) {
-                    a[q] = conj_(A[spos<B>(e0 + q * strideA)]);
-                    gv[q] = G[spos<B>(e0 + q * strideA)];
+                    for (int q = 0; q < B; ++q) {
+                        a[q] = conj_(A[pos(q)]);
+                        gv[q] = G[pos(q)];
+                    }
+                    T gn[R];
+                    if constexpr (std::is_same<T, float>::value && B % 2 == 0 && GS == 1) {
+                        // packed FP32x2, the same operations in the same order as below:
+                        // dW row i, columns (j, j+1); g' rows (i, i+1) from W^H's row pairs
+#pragma unroll
+                        for (int i = 0; i < B; ++i) {
+                            const float2 gi2 = make_float2(gv[i], gv[i]);
+#pragma unroll
+                            for (int j = 0; j < B; j += 2) {
+                                const float2 c = __ffma2_rn(gi2, make_float2(a[j], a[j + 1]),
+                                                            make_float2(acc[i][j], acc[i][j + 1]));
+                                acc[i][j] = c.x;
+                                acc[i][j + 1] = c.y;
+                            }
+                        }
+#pragma unroll
+                        for (int ip = 0; ip < B / 2; ++ip) {
+                            float2 sum = __fmul2_rn(WH.wp[ip * B], make_float2(gv[0], gv[0]));
+#pragma unroll
+                            for (int j = 1; j < B; ++j) sum = __ffma2_rn(WH.wp[ip * B + j], make_float2(gv[j], gv[j]), sum);
+                            gn[2 * ip] = sum.x;
+                            gn[2 * ip + 1] = sum.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int ii = 0; ii < R; ++ii) {
+                            const int i = (int)ib * R + ii;
+                            const T gi = GS == 1 ? gv[ii] : pick<T, B>(gv, i);
+                            // dW[i][j] += g[i] * conj(a[j])
+#pragma unroll
+                            for (int j = 0; j < B; ++j) acc[ii][j] = fma_acc(gi, a[j], acc[ii][j]);
+                            // g'[i] = sum_j W^H[i][j] g[j]
+                            T sum = mul(WH.w[i * B], gv[0]);
+#pragma unroll
+                            for (int j = 1; j < B; ++j) sum = fma_acc(WH.w[i * B + j], gv[j], sum);
+                            gn[ii] = sum;
+                        }
+                    }
+                    if (GS > 1) __syncwarp(__activemask());
+#pragma unroll
+                    for (int ii = 0; ii < R; ++ii) G[pos((int)ib * R + ii)] = gn[ii];
+                };
+                if (lin) {
+                    const uint32_t sb = spos<B>(e0);
+                    body([&](int q) { return sb + (uint32_t)q * step; });
+                } else {
+                    body([&](int q) { return spos<B>(e0 + (uint32_t)q * strideA); });
                 }
-                T gn[R];
-#pragma unroll
-                for (int ii = 0; ii < R; ++ii) {
-                    const int i = (int)ib * R + ii;
-                    const T gi = GS == 1 ? gv[ii] : pick<T, B>(gv, i);
-                    // dW[i][j] += g[i] * conj(a[j])
-#pragma unroll
-                    for (int j = 0; j < B; ++j) acc[ii][j] = fma_acc(gi, a[j], acc[ii][j]);
-                    // g'[i] = sum_j W^H[i][j] g[j]
-                    T sum = mul(WH.w[i * B], gv[0]);
-#pragma unroll
-                    for (int j = 1; j < B; ++j) sum = fma_acc(WH.w[i * B + j], gv[j], sum);
-                    gn[ii] = sum;
-                }
-                if (GS > 1) __syncwarp(__activemask());
-#pragma unroll
-                for (int ii = 0; ii < R; ++ii) G[spos<B>(e0 + ((int)ib * R + ii) * strideA)] = gn[ii];
             }
             __syncthreads();
         }
