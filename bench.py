@@ -54,6 +54,24 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest `value` over the ranks: the slowest rank sets the whole
+    job's time.  The value itself when world == 1."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gelems(world: int, steps: int, elems_per_step: float, seconds: float) -> float:
+    """Whole-job throughput: every rank transforms its own data (weak scaling)
+    over `seconds`, the time of the slowest rank."""
+    return world * steps * elems_per_step / seconds / 1e9
+
+
 # ------------------------------------------------------------ clocks sampler
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -253,13 +271,9 @@ def run_e2e(plan, x, dev, args, world):
     t0 = time.perf_counter()
     run(ke)
     torch.cuda.synchronize(dev)
-    el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(time.perf_counter() - t0, world, dev)
     err = float(np.linalg.norm(zh[(ke - 1) % 2].numpy() - x) / np.linalg.norm(x))
-    out = {"value": world * ke * 2 * BATCH * N / el / 1e9, "unit": "Gelem/s",
+    out = {"value": whole_job_gelems(world, ke, 2 * BATCH * N, el), "unit": "Gelem/s",
            "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes), "steps": ke,
            "api": "pinned host x -> device (copy stream), gtt_forward + gtt_inverse (compute stream), "
                   "result -> pinned host (copy stream); double-buffered across steps",
@@ -274,7 +288,7 @@ def run_e2e(plan, x, dev, args, world):
         plan.forward_host(xh.numpy(), out=yh.numpy())
         plan.inverse_host(yh.numpy(), out=zh[0].numpy())
     elh = time.perf_counter() - t0
-    out["host_buffer_calls"] = {"value": world * kh * 2 * BATCH * N / elh / 1e9, "unit": "Gelem/s",
+    out["host_buffer_calls"] = {"value": whole_job_gelems(world, kh, 2 * BATCH * N, elh), "unit": "Gelem/s",
                                 "h2d_bytes_per_step": 2 * int(x.nbytes), "d2h_bytes_per_step": 2 * int(x.nbytes),
                                 "steps": kh, "api": "gtt_forward_host + gtt_inverse_host"}
     return out
@@ -339,11 +353,7 @@ def run_gpu(args, rank, world, local_rank):
     elapsed_ms = t_start.elapsed_time(t_stop)
     tim = plan.timing()
 
-    # max over ranks
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
 
     # parity spot check of the timed output (inverse(forward(x)) ~ x)
     err = float(torch.linalg.vector_norm(zd - xd) / torch.linalg.vector_norm(xd))
@@ -397,7 +407,7 @@ def run_gpu(args, rank, world, local_rank):
                  "other": hbm_obj if intensity >= ridge else alu_obj})
 
     elapsed_s = elapsed_ms / 1e3
-    value = world * args.steps * 2 * BATCH * N / elapsed_s / 1e9
+    value = whole_job_gelems(world, args.steps, 2 * BATCH * N, elapsed_s)
     alg_bytes_step = 2 * len(passes) * bytes_per_launch  # fwd + inv
     line = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world,
