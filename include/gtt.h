@@ -66,7 +66,8 @@ typedef enum {
 
 /* Arithmetic used for the b >= 16 contractions (gtt_plan_set_precision). */
 typedef enum {
-    GTT_PREC_AUTO = 0,   /* library choice (FP32 CUDA-core)                         */
+    GTT_PREC_AUTO = 0,   /* library choice, the default: BF16X3 for b = 16 FP32 with
+                            n >= 3 (faster, and at least as accurate), else FP32      */
     GTT_PREC_FP32 = 1,   /* FP32 FMA on CUDA cores                                  */
     GTT_PREC_BF16X3 = 2  /* tcgen05 BF16 products of 3-piece splits, FP32 accumulate */
 } gtt_precision_t;
@@ -97,8 +98,12 @@ gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_d
 gtt_status_t gtt_plan_set_w(gtt_plan_t plan, const void *W);
 
 /* Select the arithmetic of the b = 16 contraction (gtt_precision_t).  Other b
- * accept GTT_PREC_AUTO and GTT_PREC_FP32 only.  GTT_PREC_BF16X3 requires b = 16
- * and dtype F32; otherwise GTT_ERR_UNSUPPORTED. */
+ * accept GTT_PREC_AUTO and GTT_PREC_FP32 only.  GTT_PREC_BF16X3 requires b = 16,
+ * dtype F32 and n >= 3; otherwise GTT_ERR_UNSUPPORTED.  The tensor-core path has
+ * one fixed schedule: gtt_plan_set_schedule and gtt_plan_set_passes install a
+ * CUDA-core schedule and so switch the plan to FP32; gtt_plan_set_pipeline
+ * only affects later CUDA-core schedules and the backward; gtt_plan_autotune
+ * leaves a tensor-core plan unchanged. */
 gtt_status_t gtt_plan_set_precision(gtt_plan_t plan, int precision);
 
 /*

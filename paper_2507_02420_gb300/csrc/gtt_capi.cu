@@ -251,6 +251,37 @@ static gtt_status_t check_device(gtt_plan_s *P) {
     return GTT_OK;
 }
 
+// AUTO's choice: the tensor-core path where it exists (b = 16, FP32, n >= 3),
+// which is faster than the CUDA-core path and at least as accurate; FP32 CUDA
+// cores everywhere else.
+static bool tc_eligible(const gtt_plan_s *P) { return P->b == 16 && P->dtype == GTT_F32 && P->n >= 3; }
+
+// Back to a CUDA-core schedule (the plan's fixed rule or its explicit passes).
+static gtt_status_t use_cuda_core(gtt_plan_s *P) {
+    if (P->precision == GTT_PREC_BF16X3) {
+        std::vector<PassPlan> passes;
+        gtt_status_t st = P->explicit_g.empty()
+                              ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
+                              : make_explicit_schedule(P, (int)P->explicit_g.size(), P->explicit_g.data(),
+                                                       P->explicit_r.data(), &passes);
+        if (st != GTT_OK) return st;
+        P->passes = passes;
+    }
+    P->precision = GTT_PREC_FP32;
+    return GTT_OK;
+}
+
+static gtt_status_t use_tensor_cores(gtt_plan_s *P) {
+    std::vector<PassPlan> passes;
+    gtt_status_t st = make_tc_schedule(P, &passes);
+    if (st != GTT_OK) return st;
+    st = tc_upload_w(P);
+    if (st != GTT_OK) return st;
+    P->passes = passes;
+    P->precision = GTT_PREC_BF16X3;
+    return GTT_OK;
+}
+
 extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W,
                                         gtt_dtype_t dtype, long long batch) {
     if (!out || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL out or W");
@@ -306,6 +337,8 @@ extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const voi
         const char *at = std::getenv("GTT_AUTOTUNE");
         if (at && std::strcmp(at, "on") == 0) autotune(P, 64);
     }
+    // the default precision (AUTO): tensor cores where they apply
+    if (tc_eligible(P) && use_tensor_cores(P) != GTT_OK) P->precision = GTT_PREC_FP32;
     *out = P;
     return GTT_OK;
 }
@@ -346,6 +379,7 @@ extern "C" gtt_status_t gtt_plan_set_passes(gtt_plan_t P, int count, const int *
     gtt_status_t st = make_explicit_schedule(P, count, digits, runs, &passes);
     if (st != GTT_OK) return st;
     P->passes = passes;
+    P->precision = GTT_PREC_FP32;  // a CUDA-core schedule
     P->explicit_g.assign(digits, digits + count);
     P->explicit_r.assign(runs, runs + count);
     return GTT_OK;
@@ -359,6 +393,7 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     P->use_tma = use_tma != 0;
     P->tma_nbuf = nbuf;
     P->bwd_ready = false;  // the backward's recompute passes follow the pipeline choice
+    if (P->precision == GTT_PREC_BF16X3) return GTT_OK;  // tensor-core passes stage their own tiles
     std::vector<PassPlan> passes;
     gtt_status_t st = P->explicit_g.empty()
                           ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
@@ -394,28 +429,11 @@ extern "C" gtt_status_t gtt_plan_check(gtt_plan_t P) {
 
 extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
-    if (precision == GTT_PREC_AUTO || precision == GTT_PREC_FP32) {
-        if (P->precision == GTT_PREC_BF16X3) {  // back to the CUDA-core schedule
-            std::vector<PassPlan> passes;
-            gtt_status_t st = P->explicit_g.empty()
-                                  ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
-                                  : make_explicit_schedule(P, (int)P->explicit_g.size(), P->explicit_g.data(),
-                                                           P->explicit_r.data(), &passes);
-            if (st != GTT_OK) return st;
-            P->passes = passes;
-        }
-        P->precision = precision;
-        return GTT_OK;
-    }
-    if (precision == GTT_PREC_BF16X3) {
-        std::vector<PassPlan> passes;
-        gtt_status_t st = make_tc_schedule(P, &passes);
-        if (st != GTT_OK) return st;
-        st = tc_upload_w(P);
-        if (st != GTT_OK) return st;
-        P->passes = passes;
-        P->precision = precision;
-        return GTT_OK;
+    if (precision == GTT_PREC_FP32) return use_cuda_core(P);
+    if (precision == GTT_PREC_BF16X3) return use_tensor_cores(P);
+    if (precision == GTT_PREC_AUTO) {
+        if (tc_eligible(P) && use_tensor_cores(P) == GTT_OK) return GTT_OK;
+        return use_cuda_core(P);
     }
     return set_error(GTT_ERR_INVALID_ARG, "unknown precision");
 }
@@ -430,6 +448,7 @@ extern "C" gtt_status_t gtt_plan_set_schedule(gtt_plan_t P, long long max_tile_b
     gtt_status_t st = make_schedule(P, max_tile_bytes, min_run_bytes, &passes);
     if (st != GTT_OK) return st;
     P->passes = passes;
+    P->precision = GTT_PREC_FP32;  // a CUDA-core schedule
     P->explicit_g.clear();
     P->explicit_r.clear();
     P->sched_tile_bytes = max_tile_bytes;
@@ -635,7 +654,8 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
     if (!P || !buf || len == 0) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or buffer");
     std::string s = "{\"b\": " + std::to_string(P->b) + ", \"n\": " + std::to_string(P->n) +
                     ", \"dtype\": " + std::to_string((int)P->dtype) + ", \"batch\": " +
-                    std::to_string(P->batch) + ", \"launches_per_transform\": " +
+                    std::to_string(P->batch) + ", \"precision\": \"" +
+                    (P->precision == GTT_PREC_BF16X3 ? "bf16x3" : "fp32") + "\", \"launches_per_transform\": " +
                     std::to_string(P->passes.size()) + ", \"passes\": [";
     for (size_t i = 0; i < P->passes.size(); ++i) {
         const PassPlan &pp = P->passes[i];

@@ -80,7 +80,11 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
         if (it == shapes.end()) {
             gtt_plan_t ph = nullptr;
             st = gtt_plan_create(&ph, R.b, R.n, R.W, R.dtype, 1);
-            if (st != GTT_OK) break;
+            if (st == GTT_OK) st = gtt_plan_set_precision(ph, GTT_PREC_FP32);  // the grouped kernel's arithmetic
+            if (st != GTT_OK) {
+                if (ph) gtt_plan_destroy(ph);
+                break;
+            }
             P = ph;
             if (P->passes.size() > (size_t)kGroupMaxPass) {
                 st = set_error(GTT_ERR_UNSUPPORTED, "schedule has too many passes for a group");

@@ -34,9 +34,8 @@ def test_chunked_passes_are_bitwise_identical(g, b, n, batch, dt, prec, tma, chu
         W = gi.haar_orthogonal(b, rng).astype(np.float32)
         x = gi.normal_x((batch, b ** n), rng, np.float32)
     plan = g.Plan(W, n, dt, batch)
+    plan.set_precision(g.PREC_BF16X3 if prec == "bf16x3" else g.PREC_FP32)
     plan.set_pipeline(tma, 2)
-    if prec == "bf16x3":
-        plan.set_precision(g.PREC_BF16X3)
     xd = torch.from_numpy(x).cuda()
     passes = plan.describe()["passes"]
     if not chunk.startswith("item") and len(passes) < 2:

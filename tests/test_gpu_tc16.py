@@ -70,6 +70,7 @@ def test_b16_n6_batch64_bf16x3_full_size_sampled(g):
     torch.cuda.synchronize()
     plan.check()
     plan32 = g.Plan(W, 6, "f32", 64)
+    plan32.set_precision(g.PREC_FP32)
     y32 = plan32.forward(xd)
     torch.cuda.synchronize()
     for item in (0, 21, 42, 63):
@@ -104,3 +105,35 @@ def test_bf16x3_rejected_where_unsupported(g):
         with pytest.raises(g.GTTError) as ei:
             plan.set_precision(g.PREC_BF16X3)
         assert ei.value.status == 2
+
+
+def test_auto_precision_picks_tensor_cores_for_b16_fp32(g):
+    """The default (AUTO) runs b = 16 FP32 transforms with n >= 3 on the
+    tensor-core path and everything else on CUDA cores; explicit CUDA-core
+    schedules switch a plan to FP32."""
+    rng = np.random.default_rng(9400)
+    cases = [(16, 4, "f32", True), (16, 6, "f32", True), (16, 2, "f32", False),
+             (16, 3, "c64", False), (8, 5, "f32", False)]
+    for b, n, dt, tc in cases:
+        if dt == "c64":
+            W = gi.haar_unitary(b, rng).astype(np.complex64)
+            x = gi.complex_normal_x((2, b ** n), rng, np.complex64)
+        else:
+            W = gi.haar_orthogonal(b, rng).astype(np.float32)
+            x = gi.normal_x((2, b ** n), rng, np.float32)
+        plan = g.Plan(W, n, dt, 2)
+        d = plan.describe()
+        assert (d["precision"] == "bf16x3") == tc, (b, n, dt, d["precision"])
+        assert any("tc16" in p["kernel"] for p in d["passes"]) == tc
+        y = plan.forward(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        up = (lambda a: a.astype(np.complex128)) if dt == "c64" else (lambda a: a.astype(np.float64))
+        ref = oracle.modes(up(W), up(x))
+        assert np.linalg.norm(up(y.cpu().numpy()) - ref) / np.linalg.norm(ref) <= 1e-6, (b, n, dt)
+        if tc:
+            plan.set_pipeline(True, 3)           # keeps the tensor-core schedule
+            assert plan.describe()["precision"] == "bf16x3"
+            plan.autotune(8)                     # a tensor-core plan is left as it is
+            assert plan.describe()["precision"] == "bf16x3"
+            plan.set_schedule(16384, 128)        # a CUDA-core schedule: FP32
+            assert plan.describe()["precision"] == "fp32"

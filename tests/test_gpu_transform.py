@@ -133,6 +133,7 @@ def test_b16_n6_batch64_f32_full_size_sampled(g):
     GPU; items 0, 21, 42, 63 are checked against the oracle (rel-L2 <= 1e-6)."""
     W, x = gi.config_inputs(2)
     plan = g.Plan(W, 6, "f32", 64)
+    plan.set_precision(g.PREC_FP32)
     xd = torch.from_numpy(x).cuda()
     y = plan.forward(xd)
     torch.cuda.synchronize()
