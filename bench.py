@@ -540,8 +540,27 @@ def extra_grouped(g, dev, hbm, reps=10):
             "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9}
 
 
+def extra_filter(g, dev, hbm, reps=10):
+    """Natural-order low-pass filter (gtt_filter, Sec. 4.3.2) on b = 4, n = 13,
+    complex64, cut N / 2: forward passes, write-only zeroing of the masked
+    half, adjoint passes; against forward + inverse on the same plan."""
+    import torch
+    W, x = gi.config_inputs(1)
+    plan = g.Plan(W, NDIG, "c64", BATCH)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.empty_like(xd)
+    tf = _time_device(lambda: plan.filter(xd, N // 2, True, out=yd), reps=reps)
+    tp = _time_device(lambda: (plan.forward(xd, out=yd), plan.inverse(yd, out=yd)), reps=reps)
+    plan.check()
+    res = {"ms": tf * 1e3, "gelem_s": BATCH * N / tf / 1e9, "cut": N // 2,
+           "forward_plus_inverse_ms": tp * 1e3, "overhead_vs_forward_plus_inverse": tf / tp - 1}
+    del xd, yd, plan
+    torch.cuda.empty_cache()
+    return res
+
+
 EXTRAS = {"b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_train_step", extra_train),
-          "grouped": ("grouped_1000_uneven", extra_grouped)}
+          "grouped": ("grouped_1000_uneven", extra_grouped), "filter": ("b4_n13_c64_lowpass_filter", extra_filter)}
 
 
 def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64):

@@ -236,6 +236,20 @@ gtt_status_t gtt_backward_noalloc(gtt_plan_t plan, const void *x_saved, const vo
                                   void *dW, gtt_stream_t stream);
 
 /*
+ * gtt_filter -- natural-order spectral filtering (Sec. 4.3.2, the classical
+ * reading of Algorithm 3): y = G_N^dagger (mask * G_N x) for every vector of
+ * the batch, where the mask keeps the coefficients of index p < cut
+ * (keep_low != 0, low-pass) or p >= cut (keep_low == 0, high-pass) and zeroes
+ * the others; the index is the natural ordering of the spectrum.  x and y are
+ * device buffers of batch*N elements with the plan's conventions (y == x is
+ * allowed).  y holds the spectrum between the two transforms; the masked
+ * range is zeroed by a write-only kernel.  Errors: GTT_ERR_INVALID_ARG (NULL or
+ * misaligned pointers, cut outside [0, N]), GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_filter(gtt_plan_t plan, const void *x, void *y, long long cut, int keep_low,
+                        gtt_stream_t stream);
+
+/*
  * gtt_forward_host / gtt_inverse_host -- the same transforms on HOST buffers:
  * copy x (batch*N elements) to plan-owned device memory, transform, copy the
  * result back into y, and wait for `stream`.  Host buffers may be pageable;

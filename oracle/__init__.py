@@ -15,6 +15,10 @@ Routes (each cites the passage it follows; the C source has the details):
 * ``modes(W, x)``           -- mode-by-mode loop, digit 0 first (Sec. 3.1 cost
                                structure); the timed CPU baseline
 * ``adjoint(W, y)``         -- G_N^dagger y = (W^H)^{(x)n} y (Sec. 4 inverse)
+* ``filter(W, x, cut, low)`` -- natural-order filtering (Sec. 4.3.2): the
+                               spectrum G_N x, coefficients with index >= cut
+                               (low-pass) or < cut (high-pass) set to zero,
+                               then G_N^dagger
 * ``grad(W, x, dy)``        -- (dx, dW) of y = G_N x for a real loss, PyTorch's
                                conjugate convention (no counterpart in the paper)
 * ``fd_grad_*``             -- central finite differences of a real loss
@@ -190,6 +194,16 @@ def adjoint(W, y, threads: int | None = None) -> np.ndarray:
     fn = _load().oracle_adjoint_r if real else _load().oracle_adjoint_c
     _check(fn(b, n, _ptr(W), _batched(y, b ** n), _ptr(y), _ptr(x), threads), "adjoint")
     return x
+
+
+def filter(W, x, cut: int, keep_low: bool = True, threads: int | None = None) -> np.ndarray:
+    """Natural-order spectral filter of Sec. 4.3.2: spectrum s = G_N x; keep
+    the coefficients s[p] with p < cut (keep_low) or p >= cut (high-pass),
+    zero the others, per vector of the batch; return G_N^dagger of the result."""
+    s = modes(W, x, threads=threads)
+    p = np.arange(s.shape[-1])
+    keep = p < cut if keep_low else p >= cut
+    return adjoint(W, np.where(keep, s, 0), threads=threads)
 
 
 def grad(W, x, dy, threads: int | None = None):

@@ -34,6 +34,7 @@ SIGNATURES = {
     "gtt_inverse": (_I, [_P, _P, _P, _P]),
     "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "gtt_backward_noalloc": (_I, [_P, _P, _P, _P, _P, _P]),
+    "gtt_filter": (_I, [_P, _P, _P, _LL, _I, _P]),
     "gtt_forward_host": (_I, [_P, _P, _P, _P]),
     "gtt_inverse_host": (_I, [_P, _P, _P, _P]),
     "gtt_plan_describe": (_I, [_P, ctypes.c_char_p, _S]),

@@ -163,6 +163,17 @@ class Plan:
               "gtt_inverse")
         return x
 
+    def filter(self, x: torch.Tensor, cut: int, keep_low: bool = True, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+        """gtt_filter: G_N^dagger (mask * G_N x), keeping spectrum indices p < cut
+        (keep_low) or p >= cut, for every vector of the batch."""
+        self._check_dev(x, "x")
+        y = torch.empty_like(x) if out is None else out
+        self._check_dev(y, "out")
+        check(self._lib.gtt_filter(self._h, x.data_ptr(), y.data_ptr(), int(cut), int(bool(keep_low)),
+                                   _stream_ptr(stream)), "gtt_filter")
+        return y
+
     def backward(self, x: torch.Tensor, dy: torch.Tensor, need_dx: bool = True,
                  need_dW: bool = True, stream=None):
         self._check_dev(x, "x")

@@ -131,6 +131,12 @@ def test_e10_natural_order_filter(golden):
     high = oracle.adjoint(W, np.where(idx >= c, spec, 0))
     np.testing.assert_allclose(low.real, g["low"], atol=5.1e-5)
     np.testing.assert_allclose(high.real, g["high"], atol=5.1e-5)
+    # the oracle's filter route gives the printed outputs too
+    np.testing.assert_allclose(oracle.filter(W, psi, c, True).real, g["low"], atol=5.1e-5)
+    np.testing.assert_allclose(oracle.filter(W, psi, c, False).real, g["high"], atol=5.1e-5)
+    # low + high = G^dagger G psi = psi for unitary W (the masks partition the spectrum)
+    np.testing.assert_allclose(oracle.filter(W, psi, c, True) + oracle.filter(W, psi, c, False), psi,
+                               atol=1e-14)
     # Sec. 4.3.2 also transforms the outputs back: the masks are recovered
     np.testing.assert_allclose(oracle.modes(W, low), np.where(idx < c, spec, 0), atol=1e-14)
 
