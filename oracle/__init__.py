@@ -15,6 +15,11 @@ Routes (each cites the passage it follows; the C source has the details):
 * ``modes(W, x)``           -- mode-by-mode loop, digit 0 first (Sec. 3.1 cost
                                structure); the timed CPU baseline
 * ``adjoint(W, y)``         -- G_N^dagger y = (W^H)^{(x)n} y (Sec. 4 inverse)
+* ``topk(W, x, k)``         -- compression step of Sec. 4.1.5: the k
+                               coefficients of largest magnitude of G_N x per
+                               vector, |c| descending, ties by larger index
+* ``reconstruct(W, i, v, N)`` -- decompression: G_N^dagger of the spectrum
+                               holding v at i, zero elsewhere
 * ``filter(W, x, cut, low)`` -- natural-order filtering (Sec. 4.3.2): the
                                spectrum G_N x, coefficients with index >= cut
                                (low-pass) or < cut (high-pass) set to zero,
@@ -194,6 +199,27 @@ def adjoint(W, y, threads: int | None = None) -> np.ndarray:
     fn = _load().oracle_adjoint_r if real else _load().oracle_adjoint_c
     _check(fn(b, n, _ptr(W), _batched(y, b ** n), _ptr(y), _ptr(x), threads), "adjoint")
     return x
+
+
+def topk(W, x, k: int, threads: int | None = None):
+    """Compression step of Sec. 4.1.5: the spectrum c = G_N x and, per vector,
+    the k coefficients of largest |c|, ordered by |c| descending and, between
+    equal magnitudes, by the larger index first.  Returns (indices, values),
+    both [batch, k]."""
+    c = np.atleast_2d(modes(W, x, threads=threads))
+    mag = c.real ** 2 + c.imag ** 2 if np.iscomplexobj(c) else c * c
+    idx = np.arange(c.shape[-1])
+    order = np.stack([np.lexsort((-idx, -m))[:k] for m in mag])
+    return order, np.take_along_axis(c, order, axis=1)
+
+
+def reconstruct(W, indices, values, N: int, threads: int | None = None) -> np.ndarray:
+    """Decompression: G_N^dagger of the spectrum that holds `values` at
+    `indices` (both [batch, k]) and zero elsewhere."""
+    values = np.atleast_2d(values)
+    spec = np.zeros((values.shape[0], N), dtype=np.result_type(values, np.float64))
+    np.put_along_axis(spec, np.atleast_2d(indices), values, axis=1)
+    return adjoint(W, spec, threads=threads)
 
 
 def filter(W, x, cut: int, keep_low: bool = True, threads: int | None = None) -> np.ndarray:

@@ -11,3 +11,4 @@ from ._lib import GTTError, LIB_PATH, load  # noqa: F401
 from .autograd import GTTFunction, gtt  # noqa: F401
 from .api import autotune_cache_load, autotune_cache_save, selftest_bounded_wait  # noqa: F401
 from .group import Group  # noqa: F401
+from . import params  # noqa: F401

@@ -116,6 +116,53 @@ def test_e3_compression_example(golden):
     np.testing.assert_allclose(oracle.modes(gi.hadamard_w(True), g["S1"]), g["H_S1"], atol=2.5e-3)
 
 
+def test_e3_e5_topk_compression(golden):
+    """Sec. 4.1.5, k = 2: the retained index sets and the fidelity table.  The
+    re-normalised truncation has fidelity F = sum over the kept |c|^2; the
+    printed Hadamard column is F and the printed GTT column is F^2 (the table
+    is inconsistent; both are pinned as printed).  The inputs are printed to 3
+    decimals, so the fidelities agree to 1e-3."""
+    g1 = golden("e3_compression_u3_n3.txt")
+    g = golden("e3_e5_compression_fidelity_k2.txt")
+    W = gi.u3(*g1["theta_phi_lambda"])
+    H = gi.hadamard_w(True)
+    states = [g1["S1"], g["S2"], g["S3"]]
+    for row, s in enumerate(states):
+        s = s / np.linalg.norm(s)
+        for T, col, squared in ((W, "gtt_fidelity", True), (H, "hadamard_fidelity", False)):
+            idx, val = oracle.topk(T, s, 2)
+            F = float(np.sum(np.abs(val) ** 2))
+            assert abs((F * F if squared else F) - g[col][row]) <= 1e-3, (row, col, F)
+            # the reconstruction from the kept pair, re-normalised, has fidelity F
+            rec = oracle.reconstruct(T, idx, val, 8)[0]
+            rec = rec / np.linalg.norm(rec)
+            assert abs(abs(np.vdot(s, rec)) ** 2 - F) <= 1e-12
+        if row == 0:
+            np.testing.assert_array_equal(oracle.topk(W, s, 2)[0][0], g["S1_gtt_indices"].astype(int))
+        else:   # S2, S3: the Hadamard spectrum has no ties among its top two
+            np.testing.assert_array_equal(oracle.topk(H, s, 2)[0][0], g["S1_hadamard_indices"].astype(int))
+            np.testing.assert_array_equal(oracle.topk(W, s, 2)[0][0], g["S1_gtt_indices"].astype(int))
+
+
+def test_topk_order_and_tie_break():
+    """Largest |c| first; equal magnitudes keep the larger index first (the
+    printed Hadamard choice [7 6] for S1 where indices 5 and 6 tie exactly)."""
+    # H/sqrt(2) on e_0: every coefficient has magnitude 2^(-n/2): all ties
+    idx, val = oracle.topk(gi.hadamard_w(True), np.eye(16)[0], 5)
+    np.testing.assert_array_equal(idx[0], [15, 14, 13, 12, 11])
+    rng = np.random.default_rng(77)
+    W = gi.haar_unitary(3, rng)
+    x = gi.complex_normal_x((2, 81), rng, np.complex128)
+    idx, val = oracle.topk(W, x, 81)
+    c = oracle.modes(W, x)
+    for b in range(2):
+        mags = np.abs(val[b])
+        assert np.all(np.diff(mags) <= 1e-15)
+        np.testing.assert_array_equal(np.sort(idx[b]), np.arange(81))   # k = N keeps everything
+    np.testing.assert_allclose(oracle.reconstruct(W, idx, val, 81), x, atol=1e-13)
+    np.testing.assert_allclose(np.take_along_axis(c, idx, axis=1), val)
+
+
 def test_e10_natural_order_filter(golden):
     """Sec. 4.3.2: spectrum of the normalised signal under U3(pi/4, 0, pi), and
     the low/high outputs G^dagger(mask * spectrum) with cutoff c = 4."""
