@@ -559,8 +559,31 @@ def extra_filter(g, dev, hbm, reps=10):
     return res
 
 
+def extra_codec(g, dev, hbm, reps=10, k=1024):
+    """Top-k compression codec (gtt_compress / gtt_decompress, Sec. 4.1.5) on
+    b = 4, n = 13, complex64, k = 1024: forward + radix select + sort, and
+    zero + scatter + adjoint."""
+    import torch
+    W, x = gi.config_inputs(1)
+    plan = g.Plan(W, NDIG, "c64", BATCH)
+    xd = torch.from_numpy(x).to(dev)
+    spec = torch.empty_like(xd)
+    idx, val = plan.compress(xd, k, spectrum=spec)
+    yd = torch.empty_like(xd)
+    tc = _time_device(lambda: plan.compress(xd, k, spectrum=spec), reps=reps)
+    td = _time_device(lambda: plan.decompress(idx, val, out=yd), reps=reps)
+    plan.check()
+    F = float((val.abs() ** 2).sum() / (xd.abs() ** 2).sum())
+    res = {"k": k, "compress_ms": tc * 1e3, "decompress_ms": td * 1e3,
+           "compress_gelem_s": BATCH * N / tc / 1e9, "kept_energy_fraction": F}
+    del xd, spec, yd, plan
+    torch.cuda.empty_cache()
+    return res
+
+
 EXTRAS = {"b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_train_step", extra_train),
-          "grouped": ("grouped_1000_uneven", extra_grouped), "filter": ("b4_n13_c64_lowpass_filter", extra_filter)}
+          "grouped": ("grouped_1000_uneven", extra_grouped), "filter": ("b4_n13_c64_lowpass_filter", extra_filter),
+          "codec": ("b4_n13_c64_topk_codec", extra_codec)}
 
 
 def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64):

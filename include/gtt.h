@@ -250,6 +250,28 @@ gtt_status_t gtt_filter(gtt_plan_t plan, const void *x, void *y, long long cut, 
                         gtt_stream_t stream);
 
 /*
+ * gtt_compress -- the classical steps of the compression protocol of
+ * Sec. 4.1.5: spectrum = G_N x (device, batch*N elements, may equal x), then
+ * for every vector the k coefficients of largest magnitude: indices[v*k + j]
+ * (device int64) and values[v*k + j] (device, the plan's element type), j
+ * ordered by |c| descending and, between equal magnitudes, by the larger
+ * index first.  |c|^2 is computed in the plan's real precision with
+ * round-to-nearest products and sum (no fused multiply-add).  1 <= k <=
+ * min(N, 4096).  The first call allocates a plan-owned selection workspace.
+ * Errors: GTT_ERR_INVALID_ARG (NULL or misaligned pointers, k out of range),
+ * GTT_ERR_UNSUPPORTED (I32), GTT_ERR_ALLOC, GTT_ERR_CUDA.
+ *
+ * gtt_decompress -- the reconstruction: y = G_N^dagger s for every vector,
+ * where s holds values[v*k + j] at index indices[v*k + j] and zero elsewhere
+ * (indices outside [0, N) are skipped; the result is not re-normalised).
+ * y: device, batch*N elements.  Same errors.
+ */
+gtt_status_t gtt_compress(gtt_plan_t plan, const void *x, void *spectrum, long long k, long long *indices,
+                          void *values, gtt_stream_t stream);
+gtt_status_t gtt_decompress(gtt_plan_t plan, const long long *indices, const void *values, long long k, void *y,
+                            gtt_stream_t stream);
+
+/*
  * gtt_forward_host / gtt_inverse_host -- the same transforms on HOST buffers:
  * copy x (batch*N elements) to plan-owned device memory, transform, copy the
  * result back into y, and wait for `stream`.  Host buffers may be pageable;

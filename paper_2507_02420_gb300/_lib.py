@@ -35,6 +35,8 @@ SIGNATURES = {
     "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "gtt_backward_noalloc": (_I, [_P, _P, _P, _P, _P, _P]),
     "gtt_filter": (_I, [_P, _P, _P, _LL, _I, _P]),
+    "gtt_compress": (_I, [_P, _P, _P, _LL, _P, _P, _P]),
+    "gtt_decompress": (_I, [_P, _P, _P, _LL, _P, _P]),
     "gtt_forward_host": (_I, [_P, _P, _P, _P]),
     "gtt_inverse_host": (_I, [_P, _P, _P, _P]),
     "gtt_plan_describe": (_I, [_P, ctypes.c_char_p, _S]),

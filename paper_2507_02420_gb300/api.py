@@ -174,6 +174,36 @@ class Plan:
                                    _stream_ptr(stream)), "gtt_filter")
         return y
 
+    def compress(self, x: torch.Tensor, k: int, spectrum: torch.Tensor | None = None, stream=None):
+        """gtt_compress: (indices [batch, k] int64, values [batch, k]) of the k
+        largest-magnitude coefficients of G_N x per vector; the spectrum is
+        written to `spectrum` (a new tensor when None; may be x)."""
+        self._check_dev(x, "x")
+        spec = torch.empty_like(x) if spectrum is None else spectrum
+        self._check_dev(spec, "spectrum")
+        shape = (self.batch, int(k))
+        idx = torch.empty(shape, dtype=torch.int64, device=x.device)
+        val = torch.empty(shape, dtype=self.torch_dtype, device=x.device)
+        check(self._lib.gtt_compress(self._h, x.data_ptr(), spec.data_ptr(), int(k), idx.data_ptr(),
+                                     val.data_ptr(), _stream_ptr(stream)), "gtt_compress")
+        return idx, val
+
+    def decompress(self, indices: torch.Tensor, values: torch.Tensor, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        """gtt_decompress: G_N^dagger of the spectrum holding `values` at `indices`."""
+        if indices.dtype != torch.int64 or not indices.is_cuda or not indices.is_contiguous():
+            raise TypeError("indices must be a contiguous CUDA int64 tensor")
+        if values.dtype != self.torch_dtype or not values.is_cuda or not values.is_contiguous():
+            raise TypeError(f"values must be a contiguous CUDA {self.torch_dtype} tensor")
+        k = int(indices.shape[-1])
+        if indices.numel() != self.batch * k or values.numel() != self.batch * k:
+            raise ValueError("indices and values must be [batch, k]")
+        y = torch.empty((self.batch, self.N), dtype=self.torch_dtype, device=values.device) if out is None else out
+        self._check_dev(y, "out")
+        check(self._lib.gtt_decompress(self._h, indices.data_ptr(), values.data_ptr(), k, y.data_ptr(),
+                                       _stream_ptr(stream)), "gtt_decompress")
+        return y
+
     def backward(self, x: torch.Tensor, dy: torch.Tensor, need_dx: bool = True,
                  need_dW: bool = True, stream=None):
         self._check_dev(x, "x")

@@ -688,6 +688,7 @@ extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
     if (P->ws_grad) cudaFree(P->ws_grad);
     if (P->ws_ck) cudaFree(P->ws_ck);
     if (P->ws_dw) cudaFree(P->ws_dw);
+    if (P->ws_topk) cudaFree(P->ws_topk);
     for (TimingRecord &r : P->pending) {
         cudaEventDestroy(r.start);
         cudaEventDestroy(r.stop);

@@ -30,6 +30,20 @@ __global__ void __launch_bounds__(256) gtt_zero_range_kernel(uint32_t *data, lon
     }
 }
 
+gtt_status_t zero_range(gtt_plan_s *P, void *y, long long lo_el, long long hi_el, cudaStream_t s) {
+    if (hi_el <= lo_el) return GTT_OK;
+    const long long wpe = P->es / 4;  // 32-bit words per element
+    long long row = P->N * wpe, lo = lo_el * wpe, hi = hi_el * wpe;
+    const bool vec = row % 4 == 0 && lo % 4 == 0 && hi % 4 == 0;
+    const long long units = P->batch * (hi - lo) / (vec ? 4 : 1);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((units + 255) / 256, 8ll * P->num_sms));
+    uint32_t *d = static_cast<uint32_t *>(y);
+    long long items = P->batch;
+    void *args[5] = {(void *)&d, (void *)&items, (void *)&row, (void *)&lo, (void *)&hi};
+    const void *k = vec ? (const void *)&gtt_zero_range_kernel<4> : (const void *)&gtt_zero_range_kernel<1>;
+    return launch_timed(P, k, dim3(grid), dim3(256), args, 0, s, "gtt_zero_range_kernel");
+}
+
 } // namespace gtt
 
 using namespace gtt;
@@ -50,20 +64,8 @@ extern "C" gtt_status_t gtt_filter(gtt_plan_t P, const void *x, void *y, long lo
     gtt_status_t st = run_passes(P, P->Wf, x, y, s);
     if (st != GTT_OK) return st;
     // zero the masked coefficients: [cut, N) for a low-pass, [0, cut) for a high-pass
-    const long long lo_el = keep_low ? cut : 0, hi_el = keep_low ? P->N : cut;
-    if (hi_el > lo_el) {
-        const long long wpe = P->es / 4;  // 32-bit words per element
-        const long long row = P->N * wpe, lo = lo_el * wpe, hi = hi_el * wpe;
-        const bool vec = row % 4 == 0 && lo % 4 == 0 && hi % 4 == 0;
-        const long long units = P->batch * (hi - lo) / (vec ? 4 : 1);
-        const int grid = (int)std::max<long long>(1, std::min<long long>((units + 255) / 256, 8ll * P->num_sms));
-        uint32_t *d = static_cast<uint32_t *>(y);
-        long long items = P->batch;
-        void *args[5] = {(void *)&d, (void *)&items, (void *)&row, (void *)&lo, (void *)&hi};
-        const void *k = vec ? (const void *)&gtt_zero_range_kernel<4> : (const void *)&gtt_zero_range_kernel<1>;
-        st = launch_timed(P, k, dim3(grid), dim3(256), args, 0, s, "gtt_zero_range_kernel");
-        if (st != GTT_OK) return st;
-    }
+    st = keep_low ? zero_range(P, y, cut, P->N, s) : zero_range(P, y, 0, cut, s);
+    if (st != GTT_OK) return st;
     // back to the signal domain
     return run_passes(P, P->Wa, y, y, s);
 }

@@ -98,6 +98,8 @@ struct gtt_plan_s {
     bool bwd_ready = false;
     void *ws_grad = nullptr, *ws_ck = nullptr, *ws_dw = nullptr;  // backward workspace
     size_t ws_grad_bytes = 0, ws_ck_bytes = 0, ws_dw_bytes = 0;
+    void *ws_topk = nullptr;                                        // top-k selection workspace
+    size_t ws_topk_bytes = 0;
     bool use_tma = true;                 // TMA-pipelined passes where the geometry allows
     int tma_nbuf = 2;                    // shared-memory buffers per CTA in TMA passes
     long long sched_tile_bytes = 0, sched_run_bytes = 0;  // limits of the current schedule
@@ -134,6 +136,9 @@ gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, v
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
                      void *out, cudaStream_t stream, long long tile_begin, long long tile_end);
+// Zero elements [lo, hi) of every vector of y (batch x N, the plan's element
+// type) with a write-only kernel.
+gtt_status_t zero_range(gtt_plan_s *P, void *y, long long lo, long long hi, cudaStream_t s);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
 } // namespace gtt

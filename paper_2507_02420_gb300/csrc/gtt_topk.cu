@@ -1,0 +1,351 @@
+// Top-k compression codec of Sec. 4.1.5 (its classical steps): the spectrum
+// c = G_N x, the k coefficients of largest magnitude of every vector (as
+// (index, value) pairs, ordered by |c| descending and, between equal
+// magnitudes, by the larger index first), and the reconstruction
+// G_N^dagger of the spectrum that holds only those pairs.
+//
+// Selection: every coefficient gets the composite key (|c|^2 bits, index).
+// |c|^2 >= 0, so its IEEE bit pattern orders like the value; the index makes
+// every key distinct and ranks equal magnitudes by the larger index.  A radix
+// select over 8-bit digits of the composite key, most significant first,
+// finds for every vector the smallest key T among its k largest: each pass
+// histograms the digit of the keys that still match the chosen prefix and
+// picks the digit at which the count from the top reaches the number still
+// needed.  A vector is finished once the chosen bucket holds exactly that
+// number (T's lower bits are then zero), at the latest after the last digit.
+// The coefficients with key >= T are collected (exactly k), one CTA per
+// vector sorts them by key descending, and the values are gathered.
+// |c|^2 is formed with explicit round-to-nearest products and sum (no fused
+// multiply-add), so the decision can be reproduced in the same precision.
+#include <algorithm>
+
+#include "gtt_plan.h"
+#include "gtt_types.cuh"
+
+namespace gtt {
+
+constexpr int kTopkMax = 4096;   // k per vector (one CTA sorts them in shared memory)
+constexpr int kTopkSortThreads = 1024;
+
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> {
+    using K = uint32_t;
+    static __device__ __forceinline__ K key(float v) { return __float_as_uint(__fmul_rn(v, v)); }
+};
+template <> struct KeyOf<c64> {
+    using K = uint32_t;
+    static __device__ __forceinline__ K key(c64 v) {
+        return __float_as_uint(__fadd_rn(__fmul_rn(v.re, v.re), __fmul_rn(v.im, v.im)));
+    }
+};
+template <> struct KeyOf<double> {
+    using K = unsigned long long;
+    static __device__ __forceinline__ K key(double v) { return (K)__double_as_longlong(__dmul_rn(v, v)); }
+};
+template <> struct KeyOf<c128> {
+    using K = unsigned long long;
+    static __device__ __forceinline__ K key(c128 v) {
+        return (K)__double_as_longlong(__dadd_rn(__dmul_rn(v.re, v.re), __dmul_rn(v.im, v.im)));
+    }
+};
+
+struct TopkState {
+    unsigned long long key_prefix;  // chosen key bits (lower bits zero)
+    uint32_t idx_prefix;            // chosen index bits (lower bits zero)
+    uint32_t need;                  // how many keys of the current bucket are still to be taken
+    uint32_t done;                  // 1: the threshold T = (key_prefix, idx_prefix) is final
+    uint32_t count;                 // keys collected so far
+};
+
+// Digit `pass` of the composite key: the key's KB bits (KB / 8 digits), then
+// the index's 32 bits (4 digits), most significant first.  match: the key's
+// bits above the digit equal the prefix chosen so far.
+template <typename K>
+__device__ __forceinline__ bool digit_of(K key, uint32_t idx, int pass, const TopkState &st, uint32_t *d) {
+    constexpr int KB = 8 * (int)sizeof(K), KD = KB / 8;
+    if (pass < KD) {
+        const int shift = KB - 8 * (pass + 1);
+        const K mask = pass == 0 ? (K)0 : (K)(~(K)0) << (KB - 8 * pass);
+        if ((key & mask) != (K)st.key_prefix) return false;
+        *d = (uint32_t)(key >> shift) & 255u;
+        return true;
+    }
+    const int q = pass - KD;
+    if (key != (K)st.key_prefix) return false;
+    const uint32_t mask = q == 0 ? 0u : ~0u << (32 - 8 * q);
+    if ((idx & mask) != st.idx_prefix) return false;
+    *d = (idx >> (24 - 8 * q)) & 255u;
+    return true;
+}
+
+// Histogram of digit `pass` over the matching keys of vector blockIdx.y.
+template <typename T>
+__global__ void __launch_bounds__(256) gtt_topk_hist_kernel(const T *spec, long long N, int pass,
+                                                            const TopkState *state, uint32_t *hist) {
+    using K = typename KeyOf<T>::K;
+    const long long item = blockIdx.y;
+    const TopkState st = state[item];
+    if (st.done) return;
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const T *v = spec + item * N;
+    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < N; e += (long long)gridDim.x * 256) {
+        uint32_t d;
+        if (digit_of<K>(KeyOf<T>::key(v[e]), (uint32_t)e, pass, st, &d)) atomicAdd(&h[d], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[item * 256 + threadIdx.x], h[threadIdx.x]);
+}
+
+// Pick the digit of pass `pass` for vector blockIdx.x and clear its histogram.
+template <typename K>
+__global__ void __launch_bounds__(256) gtt_topk_scan_kernel(int pass, TopkState *state, uint32_t *hist) {
+    constexpr int KB = 8 * (int)sizeof(K), KD = KB / 8;
+    const long long item = blockIdx.x;
+    uint32_t *h = hist + item * 256;
+    if (threadIdx.x == 0 && !state[item].done) {
+        TopkState st = state[item];
+        uint32_t above = 0;
+        for (int d = 255; d >= 0; --d) {
+            const uint32_t c = h[d];
+            if (above + c >= st.need) {  // the threshold lies in bucket d
+                if (pass < KD)
+                    st.key_prefix |= (unsigned long long)d << (KB - 8 * (pass + 1));
+                else
+                    st.idx_prefix |= (uint32_t)d << (24 - 8 * (pass - KD));
+                st.need -= above;
+                if (c == st.need) st.done = 1u;  // the whole bucket is taken
+                break;
+            }
+            above += c;
+        }
+        state[item] = st;
+    }
+    __syncthreads();
+    h[threadIdx.x] = 0;
+}
+
+// Collect the keys >= T of vector blockIdx.y (exactly k of them).
+template <typename T>
+__global__ void __launch_bounds__(256) gtt_topk_collect_kernel(const T *spec, long long N, long long k,
+                                                               TopkState *state,
+                                                               typename KeyOf<T>::K *sel_key, uint32_t *sel_idx) {
+    using K = typename KeyOf<T>::K;
+    const long long item = blockIdx.y;
+    const K tk = (K)state[item].key_prefix;
+    const uint32_t ti = state[item].idx_prefix;
+    const T *v = spec + item * N;
+    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < N; e += (long long)gridDim.x * 256) {
+        const K key = KeyOf<T>::key(v[e]);
+        if (key > tk || (key == tk && (uint32_t)e >= ti)) {
+            const uint32_t slot = atomicAdd(&state[item].count, 1u);
+            if (slot < (uint32_t)k) {
+                sel_key[item * k + slot] = key;
+                sel_idx[item * k + slot] = (uint32_t)e;
+            }
+        }
+    }
+}
+
+// Sort the k collected (key, index) pairs of vector blockIdx.x by key
+// descending (bitonic, padded to a power of two with entries that sort last;
+// when P2 == size the last merge runs in output order over the whole array)
+// and write the indices and the gathered values.
+template <typename T>
+__global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_sort_kernel(const T *spec, long long N, long long k,
+                                                                         const typename KeyOf<T>::K *sel_key,
+                                                                         const uint32_t *sel_idx, long long *out_idx,
+                                                                         T *out_val) {
+    using K = typename KeyOf<T>::K;
+    constexpr uint32_t kPad = 0xFFFFFFFFu;  // index of a padding entry (real indices are < 2^32 - 1)
+    __shared__ K sk[kTopkMax];
+    __shared__ uint32_t si[kTopkMax];
+    const long long item = blockIdx.x;
+    int P2 = 1;
+    while (P2 < k) P2 <<= 1;
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        const bool ok = i < k;
+        sk[i] = ok ? sel_key[item * k + i] : (K)0;
+        si[i] = ok ? sel_idx[item * k + i] : kPad;
+    }
+    __syncthreads();
+    // "a before b" in the output order: collected pairs first, then key, then index, descending
+    auto before = [&](int a, int b) {
+        const bool va = si[a] != kPad, vb = si[b] != kPad;
+        if (va != vb) return va;
+        if (sk[a] != sk[b]) return sk[a] > sk[b];
+        return si[a] > si[b];
+    };
+    for (int size = 2; size <= P2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool desc = (i & size) == 0;  // this run sorts in output order
+                    if (desc ? before(j, i) : before(i, j)) {
+                        const K tk = sk[i];
+                        sk[i] = sk[j];
+                        sk[j] = tk;
+                        const uint32_t ti = si[i];
+                        si[i] = si[j];
+                        si[j] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        out_idx[item * k + i] = (long long)si[i];
+        out_val[item * k + i] = spec[item * N + si[i]];
+    }
+}
+
+// y[item][idx[item][j]] = val[item][j] (y zeroed beforehand).
+template <typename T>
+__global__ void __launch_bounds__(256) gtt_topk_scatter_kernel(const long long *idx, const T *val, long long k,
+                                                               long long items, long long N, T *y) {
+    const long long total = items * k;
+    for (long long u = blockIdx.x * 256ll + threadIdx.x; u < total; u += (long long)gridDim.x * 256) {
+        const long long item = u / k, i = idx[u];
+        if (i >= 0 && i < N) y[item * N + i] = val[u];  // indices outside [0, N) are skipped
+    }
+}
+
+template <typename T> struct TopkKernels {
+    static const void *hist() { return (const void *)&gtt_topk_hist_kernel<T>; }
+    static const void *scan() { return (const void *)&gtt_topk_scan_kernel<typename KeyOf<T>::K>; }
+    static const void *collect() { return (const void *)&gtt_topk_collect_kernel<T>; }
+    static const void *sort() { return (const void *)&gtt_topk_sort_kernel<T>; }
+    static const void *scatter() { return (const void *)&gtt_topk_scatter_kernel<T>; }
+    static constexpr int key_bytes = (int)sizeof(typename KeyOf<T>::K);
+};
+
+template <typename T>
+static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, long long *out_idx, void *out_val,
+                                cudaStream_t s) {
+    using TK = TopkKernels<T>;
+    const long long B = P->batch, N = P->N;
+    const int KB = TK::key_bytes;
+    // workspace: states, histograms, collected keys and indices
+    const size_t st_bytes = ((size_t)B * sizeof(TopkState) + 255) / 256 * 256;
+    const size_t h_bytes = (size_t)B * 256 * sizeof(uint32_t);
+    const size_t key_bytes = ((size_t)B * k * KB + 255) / 256 * 256;
+    const size_t need = st_bytes + h_bytes + key_bytes + (size_t)B * k * sizeof(uint32_t);
+    if (P->ws_topk_bytes < need) {
+        if (P->ws_topk) cudaFree(P->ws_topk);
+        P->ws_topk = nullptr;
+        P->ws_topk_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->ws_topk, need);
+        if (e != cudaSuccess) {
+            P->ws_topk = nullptr;
+            return set_error(GTT_ERR_ALLOC, std::string("top-k workspace: ") + cudaGetErrorString(e));
+        }
+        P->ws_topk_bytes = need;
+    }
+    unsigned char *w = static_cast<unsigned char *>(P->ws_topk);
+    TopkState *state = reinterpret_cast<TopkState *>(w);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + st_bytes);
+    void *sel_key = w + st_bytes + h_bytes;
+    uint32_t *sel_idx = reinterpret_cast<uint32_t *>(w + st_bytes + h_bytes + key_bytes);
+    // initial state: nothing chosen, k needed
+    std::vector<TopkState> init((size_t)B);
+    for (TopkState &t : init) t = TopkState{0ull, 0u, (uint32_t)k, 0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(state, init.data(), (size_t)B * sizeof(TopkState), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, h_bytes, s);
+    if (e != cudaSuccess) return cuda_error(e, "top-k workspace set-up");
+    // pass geometry: blocks per vector so the whole batch fills the GPU
+    const long long per_item = std::max<long long>(1, std::min<long long>((N + 2047) / 2048,
+                                                                           (8ll * P->num_sms + B - 1) / B));
+    const dim3 grid((unsigned)per_item, (unsigned)B);
+    const int passes = KB + 4;  // key digits, then index digits
+    gtt_status_t st;
+    for (int pass = 0; pass < passes; ++pass) {
+        const void *sp = spec;
+        long long n = N;
+        int ps = pass;
+        void *hargs[5] = {(void *)&sp, (void *)&n, (void *)&ps, (void *)&state, (void *)&hist};
+        st = launch_timed(P, TK::hist(), grid, dim3(256), hargs, 0, s, "gtt_topk_hist_kernel");
+        if (st != GTT_OK) return st;
+        void *sargs[3] = {(void *)&ps, (void *)&state, (void *)&hist};
+        st = launch_timed(P, TK::scan(), dim3((unsigned)B), dim3(256), sargs, 0, s, "gtt_topk_scan_kernel");
+        if (st != GTT_OK) return st;
+    }
+    const void *sp = spec;
+    long long n = N, kk = k;
+    void *cargs[6] = {(void *)&sp, (void *)&n, (void *)&kk, (void *)&state, (void *)&sel_key, (void *)&sel_idx};
+    st = launch_timed(P, TK::collect(), grid, dim3(256), cargs, 0, s, "gtt_topk_collect_kernel");
+    if (st != GTT_OK) return st;
+    void *oargs[7] = {(void *)&sp, (void *)&n, (void *)&kk, (void *)&sel_key, (void *)&sel_idx, (void *)&out_idx,
+                      (void *)&out_val};
+    return launch_timed(P, TK::sort(), dim3((unsigned)B), dim3(kTopkSortThreads), oargs, 0, s, "gtt_topk_sort_kernel");
+}
+
+template <typename T>
+static gtt_status_t topk_scatter(gtt_plan_s *P, const long long *idx, const void *val, long long k, void *y,
+                                 cudaStream_t s) {
+    long long kk = k, items = P->batch, n = P->N;
+    const long long total = items * k;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8ll * P->num_sms));
+    void *args[6] = {(void *)&idx, (void *)&val, (void *)&kk, (void *)&items, (void *)&n, (void *)&y};
+    return launch_timed(P, TopkKernels<T>::scatter(), dim3(grid), dim3(256), args, 0, s, "gtt_topk_scatter_kernel");
+}
+
+} // namespace gtt
+
+using namespace gtt;
+
+static gtt_status_t topk_check(gtt_plan_t P, long long k) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (P->dtype == GTT_I32) return set_error(GTT_ERR_UNSUPPORTED, "top-k compression needs a floating-point dtype");
+    if (k < 1 || k > P->N || k > kTopkMax)
+        return set_error(GTT_ERR_INVALID_ARG, "k must be in [1, min(N, " + std::to_string(kTopkMax) + ")]");
+    if (P->N >= 0xFFFFFFFFll) return set_error(GTT_ERR_UNSUPPORTED, "vectors of 2^32 - 1 elements or more");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev != P->device) return set_error(GTT_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");
+    return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_compress(gtt_plan_t P, const void *x, void *spectrum, long long k, long long *indices,
+                                     void *values, gtt_stream_t stream) {
+    gtt_status_t st = topk_check(P, k);
+    if (st != GTT_OK) return st;
+    if (!x || !spectrum || !indices || !values) return set_error(GTT_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)x & 15u) || ((uintptr_t)spectrum & 15u) || ((uintptr_t)indices & 7u) ||
+        ((uintptr_t)values & 15u))
+        return set_error(GTT_ERR_INVALID_ARG, "misaligned pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_passes(P, P->Wf, x, spectrum, s);
+    if (st != GTT_OK) return st;
+    switch (P->dtype) {
+    case GTT_F32: return topk_select<float>(P, spectrum, k, indices, values, s);
+    case GTT_F64: return topk_select<double>(P, spectrum, k, indices, values, s);
+    case GTT_C64: return topk_select<c64>(P, spectrum, k, indices, values, s);
+    case GTT_C128: return topk_select<c128>(P, spectrum, k, indices, values, s);
+    default: return set_error(GTT_ERR_UNSUPPORTED, "dtype");
+    }
+}
+
+extern "C" gtt_status_t gtt_decompress(gtt_plan_t P, const long long *indices, const void *values, long long k,
+                                       void *y, gtt_stream_t stream) {
+    gtt_status_t st = topk_check(P, k);
+    if (st != GTT_OK) return st;
+    if (!indices || !values || !y) return set_error(GTT_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)y & 15u) || ((uintptr_t)indices & 7u) || ((uintptr_t)values & 15u))
+        return set_error(GTT_ERR_INVALID_ARG, "misaligned pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = zero_range(P, y, 0, P->N, s);
+    if (st != GTT_OK) return st;
+    switch (P->dtype) {
+    case GTT_F32: st = topk_scatter<float>(P, indices, values, k, y, s); break;
+    case GTT_F64: st = topk_scatter<double>(P, indices, values, k, y, s); break;
+    case GTT_C64: st = topk_scatter<c64>(P, indices, values, k, y, s); break;
+    case GTT_C128: st = topk_scatter<c128>(P, indices, values, k, y, s); break;
+    default: st = set_error(GTT_ERR_UNSUPPORTED, "dtype");
+    }
+    if (st != GTT_OK) return st;
+    return run_passes(P, P->Wa, y, y, s);
+}
