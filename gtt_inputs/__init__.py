@@ -184,3 +184,14 @@ def config3_mask(batch: int | None = None):
     rng = np.random.default_rng(c["seed"] + 1000)
     bsz = c["batch"] if batch is None else batch
     return uniform_mask((bsz, c["b"] ** c["n"]), rng)
+
+
+def function_encoding_signal(n: int) -> np.ndarray:
+    """The test signal of the function-encoding example (Sec. 4.2): a
+    degree-7 polynomial with small sinusoidal and exponential terms on [0, 1],
+    sampled at the midpoints of N = 2^n subintervals and normalised."""
+    N = 2 ** n
+    t = (np.arange(N) + 0.5) / N
+    coef = [-978.7, 3677.0, -5575.0, 4366.0, -1875.0, 431.6, -47.57, 1.886]  # x^7 .. x^0
+    f = np.polyval(coef, t) + 0.1 * np.sin(0.1 * t) - 0.01 * np.exp(-t)
+    return f / np.linalg.norm(f)

@@ -14,8 +14,11 @@ parameters.
 """
 from __future__ import annotations
 
+import math
+
 import torch
 
+from .api import Plan
 from .autograd import gtt
 
 
@@ -37,3 +40,28 @@ def support_energy(x: torch.Tensor, W: torch.Tensor, n: int, support: torch.Tens
     c = gtt(x, W.to(x.device), n)
     kept = torch.gather(c, 1, support.to(x.device))
     return (kept.abs() ** 2).sum(dim=1)
+
+
+def fit_u3(x: torch.Tensor, n: int, k: int, steps: int = 40, lr: float = 0.5,
+           init=(math.pi / 2, 0.0, math.pi)):
+    """Gradient ascent of the compression fidelity over (theta, phi, lambda)
+    for b = 2 (step 5 of the function-encoding procedure, Sec. 4.2, with a
+    gradient method in place of a bounded quasi-Newton search).  Every step
+    takes the retained set S from gtt_compress at the current parameters and
+    the gradient of F = sum_{j in S} |(G_N x)_j|^2 from the library's backward.
+    x: [batch, 2^n] complex128 CUDA tensor of unit vectors.  The default start
+    U3(pi/2, 0, pi) is the Hadamard matrix.  Returns (parameters, fidelity of
+    every step); the fidelities are summed over the batch."""
+    t = torch.tensor(init, dtype=torch.float64, requires_grad=True)
+    plan = Plan(u3(*t.detach()), n, "c128", int(x.shape[0]))
+    history = []
+    for _ in range(steps):
+        W = u3(t[0], t[1], t[2])
+        plan.set_w(W.detach())
+        support, _ = plan.compress(x, k)
+        F = support_energy(x, W, n, support).sum()
+        history.append(float(F.detach()))
+        (grad,) = torch.autograd.grad(F, t)
+        with torch.no_grad():
+            t += lr * grad
+    return t.detach(), history
