@@ -581,9 +581,31 @@ def extra_codec(g, dev, hbm, reps=10, k=1024):
     return res
 
 
+def extra_mixed(g, dev, hbm, reps=10, batch=16):
+    """Heterogeneous transform W_0 (x) ... (x) W_8 with radices 16, 3, 9, 5, 7,
+    2, 2, 4, 11 (N = 2,661,120), complex64, batch 16: one pass per factor."""
+    import torch
+    radices = [16, 3, 9, 5, 7, 2, 2, 4, 11]
+    rng = np.random.default_rng(11)
+    Ws = [gi.haar_unitary(b, rng).astype(np.complex64) for b in radices]
+    Nm = int(np.prod(radices))
+    x = gi.complex_normal_x((batch, Nm), rng, np.complex64)
+    plan = g.Plan.mixed(Ws, "c64", batch)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.empty_like(xd)
+    t = _time_device(lambda: plan.forward(xd, out=yd), reps=reps)
+    plan.check()
+    passes = len(plan.describe()["passes"])
+    res = {"radices": radices, "batch": batch, "ms": t * 1e3, "gelem_s": batch * Nm / t / 1e9,
+           "passes": passes, "hbm_frac_if_passes_from_hbm": passes * 2 * batch * Nm * 8 / t / 1e9 / hbm}
+    del xd, yd, plan
+    torch.cuda.empty_cache()
+    return res
+
+
 EXTRAS = {"b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_train_step", extra_train),
           "grouped": ("grouped_1000_uneven", extra_grouped), "filter": ("b4_n13_c64_lowpass_filter", extra_filter),
-          "codec": ("b4_n13_c64_topk_codec", extra_codec)}
+          "codec": ("b4_n13_c64_topk_codec", extra_codec), "mixed": ("mixed_radix_9_factors_c64", extra_mixed)}
 
 
 def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64):

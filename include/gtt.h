@@ -92,6 +92,25 @@ typedef enum {
 gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_dtype_t dtype,
                              long long batch);
 
+/*
+ * gtt_plan_create_mixed -- the heterogeneous transform of the remark after
+ * Def. 2.3: G_N = W_0 (x) W_1 (x) ... (x) W_{n-1} (Kronecker product in this
+ * order) with W_k of size b_k x b_k, 2 <= b_k <= 16, N = prod b_k.  W_0 acts
+ * on the most significant index and W_{n-1} on the fastest-varying one:
+ * y[p] = sum_q prod_k W_k[p_k][q_k] with p = (...((p_0 b_1 + p_1) b_2 + p_2)...).
+ *   radices  HOST array of n ints b_0 .. b_{n-1}.
+ *   W        HOST pointer: W_0, W_1, ..., W_{n-1} back to back, each row-major
+ *            b_k x b_k of `dtype`'s element type.
+ * The plan runs one CUDA-core pass per factor (gtt_forward, gtt_inverse with
+ * the factors' adjoints, the host-buffer calls, gtt_filter, gtt_compress and
+ * gtt_decompress); gtt_plan_set_w takes the same concatenated layout.  The
+ * backward, explicit schedules and the autotuner return GTT_ERR_UNSUPPORTED
+ * for such a plan.  Errors: GTT_ERR_INVALID_ARG (NULL pointers, n < 1, a b_k
+ * outside [2, 16], sizes), GTT_ERR_ALLOC, GTT_ERR_CUDA.
+ */
+gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int *radices, const void *W, gtt_dtype_t dtype,
+                                   long long batch);
+
 /* Replace the plan's base matrix (HOST pointer, same layout and type as in
  * gtt_plan_create) without rebuilding its schedule; used when W is trained.
  * Calls already queued on a stream keep the W they were launched with. */

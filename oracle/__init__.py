@@ -20,6 +20,12 @@ Routes (each cites the passage it follows; the C source has the details):
                                vector, |c| descending, ties by larger index
 * ``reconstruct(W, i, v, N)`` -- decompression: G_N^dagger of the spectrum
                                holding v at i, zero elsewhere
+* ``kron_dense(Ws, x)``     -- the heterogeneous transform of the remark after
+                               Def. 2.3: G = W_0 (x) W_1 (x) ... (x) W_{n-1}
+                               (numpy's Kronecker product), N = prod b_k
+* ``modes_mixed(Ws, x)``    -- the same transform one factor at a time: W_k
+                               applied along axis k of x viewed as
+                               [b_0, ..., b_{n-1}] (axis 0 most significant)
 * ``filter(W, x, cut, low)`` -- natural-order filtering (Sec. 4.3.2): the
                                spectrum G_N x, coefficients with index >= cut
                                (low-pass) or < cut (high-pass) set to zero,
@@ -220,6 +226,30 @@ def reconstruct(W, indices, values, N: int, threads: int | None = None) -> np.nd
     spec = np.zeros((values.shape[0], N), dtype=np.result_type(values, np.float64))
     np.put_along_axis(spec, np.atleast_2d(indices), values, axis=1)
     return adjoint(W, spec, threads=threads)
+
+
+def kron_dense(Ws, x) -> np.ndarray:
+    """G x with G = W_0 (x) ... (x) W_{n-1} formed explicitly (small N only)."""
+    G = np.array([[1.0]])
+    for W in Ws:
+        G = np.kron(G, np.asarray(W))
+    x = np.asarray(x)
+    return x @ G.T if x.ndim > 1 else G @ x
+
+
+def modes_mixed(Ws, x) -> np.ndarray:
+    """G x for G = W_0 (x) ... (x) W_{n-1}: view each vector as the tensor
+    [b_0, ..., b_{n-1}] (row-major, so axis 0 is the most significant index)
+    and apply W_k along axis k, one factor after the other."""
+    Ws = [np.asarray(W, dtype=np.complex128 if np.iscomplexobj(W) or np.iscomplexobj(x) else np.float64)
+          for W in Ws]
+    dt = np.result_type(*Ws, np.asarray(x).dtype, np.float64)
+    x = np.atleast_2d(np.asarray(x, dtype=dt))
+    dims = [W.shape[0] for W in Ws]
+    t = x.reshape([x.shape[0]] + dims)
+    for k, W in enumerate(Ws):
+        t = np.moveaxis(np.tensordot(W, t, axes=([1], [k + 1])), 0, k + 1)
+    return t.reshape(x.shape)
 
 
 def filter(W, x, cut: int, keep_low: bool = True, threads: int | None = None) -> np.ndarray:

@@ -20,6 +20,7 @@ _S = ctypes.c_size_t
 # name -> (restype, argtypes), mirroring include/gtt.h
 SIGNATURES = {
     "gtt_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I, _LL]),
+    "gtt_plan_create_mixed": (_I, [ctypes.POINTER(_P), _I, _P, _P, _I, _LL]),
     "gtt_plan_set_precision": (_I, [_P, _I]),
     "gtt_plan_set_w": (_I, [_P, _P]),
     "gtt_plan_set_schedule": (_I, [_P, _LL, _LL]),

@@ -68,6 +68,29 @@ class Plan:
         self._h = h
         self._lib = lib
 
+    @classmethod
+    def mixed(cls, Ws, dtype=None, batch: int = 1) -> "Plan":
+        """gtt_plan_create_mixed: G = W_0 (x) W_1 (x) ... (x) W_{n-1} with W_k of
+        size b_k x b_k (W_0 acts on the most significant index), N = prod b_k."""
+        lib = load()
+        mats = [W.detach().cpu().numpy() if isinstance(W, torch.Tensor) else np.asarray(W) for W in Ws]
+        if not mats or any(m.ndim != 2 or m.shape[0] != m.shape[1] for m in mats):
+            raise ValueError("every factor must be a square matrix")
+        code = dtype_code(dtype if dtype is not None else np.result_type(*mats))
+        self = cls.__new__(cls)
+        self.radices = [int(m.shape[0]) for m in mats]
+        self.b, self.n, self.dtype, self.batch = None, len(mats), code, int(batch)
+        self.N = int(np.prod(self.radices))
+        self._rad = np.ascontiguousarray(self.radices, dtype=np.int32)
+        self._W = np.ascontiguousarray(np.concatenate([_w_host_bytes(m, code).ravel() for m in mats]))
+        h = ctypes.c_void_p()
+        check(lib.gtt_plan_create_mixed(ctypes.byref(h), self.n, self._rad.ctypes.data_as(ctypes.c_void_p),
+                                        self._W.ctypes.data_as(ctypes.c_void_p), code, self.batch),
+              "gtt_plan_create_mixed")
+        self._h = h
+        self._lib = lib
+        return self
+
     @property
     def torch_dtype(self) -> torch.dtype:
         return _TORCH_DT[self.dtype]
@@ -84,7 +107,15 @@ class Plan:
             pass
 
     def set_w(self, W):
-        """Replace W (host copy taken now) without rebuilding the schedule."""
+        """Replace W (host copy taken now) without rebuilding the schedule; for
+        a mixed plan, W is the list of factors W_0 .. W_{n-1}."""
+        if getattr(self, "radices", None) is not None:
+            mats = [w.detach().cpu().numpy() if isinstance(w, torch.Tensor) else np.asarray(w) for w in W]
+            if [m.shape for m in mats] != [(b, b) for b in self.radices]:
+                raise ValueError("factor shapes differ from the plan's")
+            self._W = np.ascontiguousarray(np.concatenate([_w_host_bytes(m, self.dtype).ravel() for m in mats]))
+            check(self._lib.gtt_plan_set_w(self._h, self._W.ctypes.data_as(ctypes.c_void_p)), "gtt_plan_set_w")
+            return
         Wn = W.detach().cpu().numpy() if isinstance(W, torch.Tensor) else np.asarray(W)
         if Wn.shape != (self.b, self.b):
             raise ValueError("W shape differs from the plan's")
@@ -209,7 +240,8 @@ class Plan:
         self._check_dev(x, "x")
         self._check_dev(dy, "dy")
         dx = torch.empty_like(dy) if need_dx else None
-        dW = torch.empty((self.b, self.b), dtype=self.torch_dtype, device=dy.device) if need_dW else None
+        # (a mixed plan has no single b; the library rejects its backward)
+        dW = torch.empty((self.b, self.b), dtype=self.torch_dtype, device=dy.device) if need_dW and self.b else None
         check(self._lib.gtt_backward(self._h, x.data_ptr(), dy.data_ptr(),
                                      dx.data_ptr() if dx is not None else None,
                                      dW.data_ptr() if dW is not None else None,

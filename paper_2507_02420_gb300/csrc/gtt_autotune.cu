@@ -257,6 +257,7 @@ using namespace gtt;
 
 extern "C" gtt_status_t gtt_plan_autotune(gtt_plan_t P, int max_candidates) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "not available for mixed-radix plans");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device)
         return set_error(GTT_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");

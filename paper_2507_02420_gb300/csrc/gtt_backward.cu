@@ -113,6 +113,7 @@ static gtt_status_t ensure_buffer(void **buf, size_t *have, size_t need, const c
 extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy, void *dx, void *dW,
                                      gtt_stream_t stream) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "not available for mixed-radix plans");
     if (P->dtype == GTT_I32) return set_error(GTT_ERR_UNSUPPORTED, "backward needs a floating-point dtype");
     if (!x || !dy) return set_error(GTT_ERR_INVALID_ARG, "NULL x or dy");
     auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };

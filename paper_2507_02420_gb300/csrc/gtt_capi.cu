@@ -40,19 +40,30 @@ static long long ipow_ll(int b, int e) {
 // consecutive blocks of b^g contiguous elements (the register stages treat the
 // block index like any digit above their window, and leave it untouched).
 gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPlan *out) {
-    const int b = P->b, es = P->es;
+    long long kblk = 1, rr = r;
+    if (m0 == 0 && r > 1) {
+        kblk = r;
+        rr = 1;
+    }
+    gtt_status_t st = build_pass_geom(P, P->b, ipow_ll(P->b, m0), g, kblk, rr, D, out);
+    if (st != GTT_OK) return st;
+    out->m0 = m0;
+    out->r = r;
+    return GTT_OK;
+}
+
+// The geometry core: digits of radix b at stride L (the product of the radices
+// below them), g of them per tile, kblk consecutive blocks per tile (L == 1),
+// runs of r elements (r divides L), register windows of D digits.
+gtt_status_t build_pass_geom(gtt_plan_s *P, int b, long long L, int g, long long kblk, long long r, int D,
+                             PassPlan *out) {
+    const int es = P->es;
     PassPlan pp;
-    pp.m0 = m0;
     pp.g = g;
     pp.D = D;
     pp.r = r;
-    long long kblk = 1;
-    if (m0 == 0 && r > 1) {
-        kblk = r;
-        r = 1;
-    }
-    const long long L = ipow_ll(b, m0), M = ipow_ll(b, g) * kblk;
-    if (L % r != 0 || g < D || g < 1) return set_error(GTT_ERR_INTERNAL, "bad pass geometry");
+    const long long M = ipow_ll(b, g) * kblk;
+    if (r < 1 || L % r != 0 || g < D || g < 1) return set_error(GTT_ERR_INTERNAL, "bad pass geometry");
     if (P->total % (M * r) != 0) return set_error(GTT_ERR_INVALID_ARG, "blocks per tile must divide the data");
     if (L / r > (1ll << 31) || M * r > (1ll << 24))
         return set_error(GTT_ERR_UNSUPPORTED, "pass geometry exceeds 32-bit tile indexing");
@@ -173,9 +184,8 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 // layout WMat<T, B>: complex64 appends the pairs (re, re) and (-im, im) of
 // every entry; FP32 appends the row pairs (W[2i][j], W[2i+1][j]) (a single
 // unused pair for odd b); other types use the element layout as it is.
-static void append_packed_pairs(gtt_plan_s *P, std::vector<unsigned char> *Wv) {
-    const int b = P->b;
-    if (P->dtype == GTT_C64) {
+static void append_packed_pairs(int dtype, int b, std::vector<unsigned char> *Wv) {
+    if (dtype == GTT_C64) {
         std::vector<float> ex;
         const float *w = reinterpret_cast<const float *>(Wv->data());
         for (int k = 0; k < b * b; ++k) {
@@ -188,7 +198,7 @@ static void append_packed_pairs(gtt_plan_s *P, std::vector<unsigned char> *Wv) {
         }
         const unsigned char *p = reinterpret_cast<const unsigned char *>(ex.data());
         Wv->insert(Wv->end(), p, p + ex.size() * sizeof(float));
-    } else if (P->dtype == GTT_F32) {
+    } else if (dtype == GTT_F32) {
         std::vector<float> ex;
         const float *w = reinterpret_cast<const float *>(Wv->data());
         if (b % 2 == 0) {
@@ -205,32 +215,48 @@ static void append_packed_pairs(gtt_plan_s *P, std::vector<unsigned char> *Wv) {
     }
 }
 
-// Copy W (host, element type) into the plan and derive W^H (the transpose,
-// conjugated for complex types), both in the kernels' parameter layout.
-static void set_w_bytes(gtt_plan_s *P, const void *W) {
-    const int b = P->b, es = P->es;
+// W (host, b x b of the element type) and W^H (the transpose, conjugated for
+// complex types), both in the kernels' parameter layout.
+static void make_w_params(int dtype, int es, int b, const void *W, std::vector<unsigned char> *Wf,
+                          std::vector<unsigned char> *Wa) {
     const size_t wbytes = (size_t)b * b * es;
-    P->Wf.assign((const unsigned char *)W, (const unsigned char *)W + wbytes);
-    P->Wa.resize(wbytes);
+    Wf->assign((const unsigned char *)W, (const unsigned char *)W + wbytes);
+    Wa->resize(wbytes);
     for (int i = 0; i < b; ++i)
         for (int j = 0; j < b; ++j) {
-            unsigned char *dst = &P->Wa[((size_t)i * b + j) * es];
-            const unsigned char *src = &P->Wf[((size_t)j * b + i) * es];
+            unsigned char *dst = &(*Wa)[((size_t)i * b + j) * es];
+            const unsigned char *src = &(*Wf)[((size_t)j * b + i) * es];
             memcpy(dst, src, es);
-            if (P->dtype == GTT_C64) {
+            if (dtype == GTT_C64) {
                 float im;
                 memcpy(&im, dst + 4, 4);
                 im = -im;
                 memcpy(dst + 4, &im, 4);
-            } else if (P->dtype == GTT_C128) {
+            } else if (dtype == GTT_C128) {
                 double im;
                 memcpy(&im, dst + 8, 8);
                 im = -im;
                 memcpy(dst + 8, &im, 8);
             }
         }
-    append_packed_pairs(P, &P->Wf);
-    append_packed_pairs(P, &P->Wa);
+    append_packed_pairs(dtype, b, Wf);
+    append_packed_pairs(dtype, b, Wa);
+}
+
+// Copy W into the plan: one matrix, or for a mixed plan the factors
+// W_0, ..., W_{n-1} back to back (each pass gets its own W and W^H).
+static void set_w_bytes(gtt_plan_s *P, const void *W) {
+    if (!P->mixed) {
+        make_w_params((int)P->dtype, P->es, P->b, W, &P->Wf, &P->Wa);
+        return;
+    }
+    const int n = P->n;
+    std::vector<size_t> off(n + 1, 0);  // byte offset of factor k
+    for (int k = 0; k < n; ++k) off[k + 1] = off[k] + (size_t)P->radices[k] * P->radices[k] * P->es;
+    for (PassPlan &pp : P->passes) {
+        const int k = pp.factor;
+        make_w_params((int)P->dtype, P->es, P->radices[k], (const unsigned char *)W + off[k], &pp.wf, &pp.wa);
+    }
 }
 
 extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
@@ -343,6 +369,73 @@ extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const voi
     return GTT_OK;
 }
 
+extern "C" gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int *radices, const void *W,
+                                              gtt_dtype_t dtype, long long batch) {
+    if (!out || !W || !radices) return set_error(GTT_ERR_INVALID_ARG, "NULL out, radices or W");
+    *out = nullptr;
+    if (n < 1) return set_error(GTT_ERR_INVALID_ARG, "n must be >= 1");
+    if (batch < 1) return set_error(GTT_ERR_INVALID_ARG, "batch must be >= 1");
+    if ((int)dtype < 0 || (int)dtype > 4) return set_error(GTT_ERR_INVALID_ARG, "unknown dtype");
+    long long N = 1;
+    for (int k = 0; k < n; ++k) {
+        if (radices[k] < 2 || radices[k] > 16) return set_error(GTT_ERR_INVALID_ARG, "every b_k must be in [2, 16]");
+        N *= radices[k];
+        if (N > (1ll << 36)) return set_error(GTT_ERR_INVALID_ARG, "N = prod b_k above 2^36");
+    }
+    if (N > (1ll << 40) / batch) return set_error(GTT_ERR_INVALID_ARG, "batch * N above 2^40");
+    gtt_plan_s *P = new (std::nothrow) gtt_plan_s();
+    if (!P) return set_error(GTT_ERR_ALLOC, "host allocation failed");
+    P->mixed = true;
+    P->radices.assign(radices, radices + n);
+    P->b = 0;  // no single base
+    P->n = n;
+    P->dtype = dtype;
+    P->batch = batch;
+    P->N = N;
+    P->total = N * batch;
+    P->es = elem_size((int)dtype);
+    P->precision = GTT_PREC_FP32;
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&P->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_error(e, "device query");
+    }
+    // one pass per factor, the fastest index first: digit j of the natural
+    // index has radix b_{n-1-j} and stride L_j = prod_{i < j} b_{n-1-i}; a tile
+    // is b rows of a run of r contiguous elements, r the product of the lowest
+    // radices that keeps the tile within the default tile size
+    const long long tmax = kDefaultTileBytes / P->es;
+    long long L = 1;
+    for (int j = 0; j < n; ++j) {
+        const int k = n - 1 - j, bj = radices[k];
+        long long r = 1;
+        for (int i = 0; i < j && r * radices[n - 1 - i] * bj <= tmax; ++i) r *= radices[n - 1 - i];
+        PassPlan pp;
+        gtt_status_t st = build_pass_geom(P, bj, L, 1, 1, r, 1, &pp);
+        if (st != GTT_OK) {
+            delete P;
+            return st;
+        }
+        pp.m0 = j;
+        pp.factor = k;
+        P->passes.push_back(pp);
+        L *= bj;
+    }
+    set_w_bytes(P, W);
+    e = cudaMalloc(&P->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->dev_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (P->dev_err) cudaFree(P->dev_err);
+        delete P;
+        return set_error(GTT_ERR_ALLOC, std::string("error flag: ") + cudaGetErrorString(e));
+    }
+    *out = P;
+    return GTT_OK;
+}
+
 namespace gtt {
 // Build an explicit schedule: pass k covers digits[k] modes with runs[k].
 gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits, const long long *runs,
@@ -375,6 +468,7 @@ gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits,
 
 extern "C" gtt_status_t gtt_plan_set_passes(gtt_plan_t P, int count, const int *digits, const long long *runs) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "explicit schedules are for single-base plans");
     std::vector<PassPlan> passes;
     gtt_status_t st = make_explicit_schedule(P, count, digits, runs, &passes);
     if (st != GTT_OK) return st;
@@ -394,6 +488,7 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     P->tma_nbuf = nbuf;
     P->bwd_ready = false;  // the backward's recompute passes follow the pipeline choice
     if (P->precision == GTT_PREC_BF16X3) return GTT_OK;  // tensor-core passes stage their own tiles
+    if (P->mixed) return GTT_OK;                          // mixed plans run the CUDA-core kernel
     std::vector<PassPlan> passes;
     gtt_status_t st = P->explicit_g.empty()
                           ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
@@ -441,6 +536,7 @@ extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
 extern "C" gtt_status_t gtt_plan_set_schedule(gtt_plan_t P, long long max_tile_bytes,
                                              long long min_run_bytes) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "schedules are for single-base plans");
     if (max_tile_bytes < 16 || max_tile_bytes > 220 * 1024 || min_run_bytes < 0 ||
         min_run_bytes > max_tile_bytes)
         return set_error(GTT_ERR_INVALID_ARG, "schedule limits out of range");
@@ -502,7 +598,7 @@ static ChunkPlan chunk_plan(const gtt_plan_s *P) {
     ChunkPlan c;
     long long C = P->chunk_elems;
     if (C == -1) C = P->total * P->es > (96ll << 20) ? (48ll << 20) / P->es : 0;  // 48 MiB chunks
-    if (C <= 0) return c;
+    if (C <= 0 || P->mixed) return c;
     int top = 0;
     long long block = 1;
     size_t prefix = 0;
@@ -527,11 +623,13 @@ static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsi
                              void *outp, cudaStream_t stream, long long tb, long long te) {
     if (pp.tc.on) return tc_run(P, pp, &Wb == &P->Wa, in, outp, stream, tb, te);
     if (pp.tma.on) return tma_run(P, pp, Wb, in, outp, stream, tb, te);
+    // a mixed plan's pass carries its own factor (W_k, or W_k^H for the adjoint)
+    const std::vector<unsigned char> &W = pp.factor < 0 ? Wb : (&Wb == &P->Wa ? pp.wa : pp.wf);
     PassParams prm = pp.params;
     prm.tile_begin = tb;
     prm.tiles = te;
     const int grid = (int)std::min<long long>(pp.grid, te - tb);
-    void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)Wb.data()};
+    void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)W.data()};
     return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
 }
 

@@ -54,6 +54,7 @@ gtt_status_t scratch_address(int dev, void **out) {
 extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const void *dy, void *dx,
                                              void *dW, gtt_stream_t stream) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "not available for mixed-radix plans");
     if (P->dtype == GTT_I32) return set_error(GTT_ERR_UNSUPPORTED, "backward needs a floating-point dtype");
     if (!x || !dy || !dx)
         return set_error(GTT_ERR_INVALID_ARG, "gtt_backward_noalloc needs x, dy and dx (dx holds its checkpoint)");

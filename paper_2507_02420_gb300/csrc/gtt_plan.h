@@ -51,6 +51,8 @@ struct PassPlan {
     std::string name;  // kernel name with its template arguments
     TmaPass tma;
     TcPass tc;
+    int factor = -1;                       // mixed plans: the factor W_k this pass applies
+    std::vector<unsigned char> wf, wa;     // mixed plans: that factor and its adjoint, parameter layout
 };
 
 // One pass of the backward schedule: the tile geometry (one stage per digit),
@@ -91,6 +93,8 @@ struct gtt_plan_s {
     gtt_dtype_t dtype = GTT_F32;
     long long batch = 0, N = 0, total = 0;
     int precision = GTT_PREC_AUTO;
+    bool mixed = false;                 // G = W_0 (x) ... (x) W_{n-1} with factor sizes `radices`
+    std::vector<int> radices;           // mixed plans: b_k of factor k (factor 0 most significant)
     std::vector<unsigned char> Wf, Wa;  // W and W^H in the element type, row-major
     std::vector<gtt::PassPlan> passes;  // forward/inverse schedule
     void *dstage = nullptr;             // device staging for the host-buffer calls
@@ -115,6 +119,8 @@ struct gtt_plan_s {
 
 namespace gtt {
 gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPlan *out);
+gtt_status_t build_pass_geom(gtt_plan_s *P, int b, long long L, int g, long long kblk, long long r, int D,
+                             PassPlan *out);
 gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long min_run_bytes,
                            std::vector<PassPlan> *out);
 // Launch `kern` with `args`, recording timing events when the plan asks for it.

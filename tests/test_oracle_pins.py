@@ -387,3 +387,26 @@ def test_pins_catch_planted_mistakes(golden):
     xi = np.random.default_rng(91).integers(-2 ** 15, 2 ** 15, size=2 ** 12)
     bad = oracle.modes_u32(np.array([[1, 1], [-1, 1]]), xi)
     assert not np.array_equal(bad, _hadamard_pm1_bigint(xi))
+
+
+# ------------------------------------------------ heterogeneous transform
+
+def test_mixed_mode_loop_is_the_kronecker_product():
+    """Remark after Def. 2.3: G = W_0 (x) ... (x) W_{n-1} with b_k x b_k
+    factors.  The mode loop equals numpy's Kronecker product for unequal
+    radices (a transposed factor or a reversed factor order fails), reduces to
+    the homogeneous transform for equal factors, and keeps norms for unitary
+    factors."""
+    rng = np.random.default_rng(31)
+    for radices in ([2, 3], [3, 2, 5], [4, 2, 3, 2], [5, 7]):
+        Ws = [gi.haar_unitary(b, rng) for b in radices]
+        N = int(np.prod(radices))
+        x = gi.complex_normal_x((3, N), rng, np.complex128)
+        ref = oracle.kron_dense(Ws, x)
+        np.testing.assert_allclose(oracle.modes_mixed(Ws, x), ref, atol=1e-12)
+        assert not np.allclose(oracle.modes_mixed(Ws[::-1], x), ref, atol=1e-6)
+        assert not np.allclose(oracle.modes_mixed([W.T for W in Ws], x), ref, atol=1e-6)
+        np.testing.assert_allclose(np.linalg.norm(ref, axis=1), np.linalg.norm(x, axis=1), rtol=1e-12)
+    W = gi.haar_unitary(3, rng)
+    x = gi.complex_normal_x((2, 3 ** 5), rng, np.complex128)
+    np.testing.assert_allclose(oracle.modes_mixed([W] * 5, x), oracle.modes(W, x), atol=1e-12)
