@@ -53,7 +53,8 @@ gtt_status_t build_pass(gtt_plan_s *P, int m0, int g, long long r, int D, PassPl
 }
 
 // The geometry core: digits of radix b at stride L (the product of the radices
-// below them), g of them per tile, kblk consecutive blocks per tile (L == 1),
+// below them), g of them per tile, kblk consecutive blocks of b^g rows per tile
+// (the rows of block hi + 1 follow those of block hi at the same stride L),
 // runs of r elements (r divides L), register windows of D digits.
 gtt_status_t build_pass_geom(gtt_plan_s *P, int b, long long L, int g, long long kblk, long long r, int D,
                              PassPlan *out) {
@@ -404,17 +405,21 @@ extern "C" gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int 
         return cuda_error(e, "device query");
     }
     // one pass per factor, the fastest index first: digit j of the natural
-    // index has radix b_{n-1-j} and stride L_j = prod_{i < j} b_{n-1-i}; a tile
-    // is b rows of a run of r contiguous elements, r the product of the lowest
-    // radices that keeps the tile within the default tile size
+    // index has radix b_{n-1-j} and stride L_j = prod_{i < j} b_{n-1-i}.  A tile
+    // is kblk consecutive blocks of b rows (a row every L elements) of a run of
+    // r contiguous elements: r the product of the lowest radices, kblk the
+    // product of the next higher ones, as far as the default tile size allows
+    // (rows kblk * b at stride L address blocks hi .. hi + kblk - 1 in turn)
     const long long tmax = kDefaultTileBytes / P->es;
+    auto rad = [&](int digit) { return (long long)radices[n - 1 - digit]; };
     long long L = 1;
     for (int j = 0; j < n; ++j) {
         const int k = n - 1 - j, bj = radices[k];
-        long long r = 1;
-        for (int i = 0; i < j && r * radices[n - 1 - i] * bj <= tmax; ++i) r *= radices[n - 1 - i];
+        long long r = 1, kblk = 1;
+        for (int i = 0; i < j && r * rad(i) * bj <= tmax; ++i) r *= rad(i);
+        for (int i = j + 1; i < n && kblk * rad(i) * bj * r <= tmax; ++i) kblk *= rad(i);
         PassPlan pp;
-        gtt_status_t st = build_pass_geom(P, bj, L, 1, 1, r, 1, &pp);
+        gtt_status_t st = build_pass_geom(P, bj, L, 1, kblk, r, 1, &pp);
         if (st != GTT_OK) {
             delete P;
             return st;
