@@ -133,7 +133,7 @@ struct TcCtx {
 // One mode of the tile in S: read fibre m, split it into three BF16 pieces
 // (the A operand), run the BF16x3 MMAs into TMEM, and write y_m back to S
 // (D < 2) or, for the last mode, straight to global memory at o[n * stride_n].
-// Returns false, uniformly across the CTA, if the MMA completion timed out.
+// Returns false in a thread whose wait for the MMA completion timed out.
 template <int D>
 __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phase, float *o, long long stride_n) {
     uint32_t off[16];
@@ -190,9 +190,10 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.bar)
                      : "memory");
     }
+    // every thread waits for the MMAs itself; an expired wait is voted on at the
+    // next tile's barrier (the CTA then stops), so no barrier is needed here
     const bool ok = mbar_wait(c.bar, phase);
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float c0[16], c1[16], c2[16];
     tmem_ld16(c.tmem_row, c0);
@@ -220,8 +221,12 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
     // the next mode issues MMAs into the same TMEM columns only after its own
     // barrier, which every thread reaches after finishing these loads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    if (D < 2) __syncthreads();  // y_m in S, visible to the next mode
-    return true;
+    // y_m in S, visible to the next mode.  Mode 0 -> mode 1 stays inside a
+    // warp: element (h2, h1, h0) is written by thread h1 + 16 h2 and read by
+    // thread h0 + 16 h2, both in warp h2 / 2.  Mode 1 -> mode 2 crosses warps.
+    if (D == 0) __syncwarp();
+    if (D == 1) __syncthreads();
+    return ok;
 }
 
 // Pass over tiles of three base-16 digits whose top G are transformed (G = 3:
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
     c.descB = umma_sdesc(smem_addr(Bw));
     c.A = A;
     uint32_t phase = 0;
-    bool failed = false;
+    bool failed = false, bad = false;
 
     const long long LM = p.L * (long long)p.M;
     const long long G0 = p.tile_begin + blockIdx.x, step = gridDim.x;
@@ -299,19 +304,18 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
     for (long long t = G0; t < p.tiles; t += step) {
         issue_load(t + 2 * step, slot == 0 ? 2 : slot - 1);
         asm volatile("cp.async.wait_group 2;" ::: "memory");  // tile t's group is complete
-        __syncthreads();
-        float *S = ring + slot * kTcTile;
-        float *o = out + tile_base(t) + (long long)rowm * p.L + colm;
-        bool ok = true;
-        if (G == 3) ok = tc_mode<0>(c, S, phase, o, stride_n);
-        if (G >= 2 && ok) ok = tc_mode<1>(c, S, phase, o, stride_n);
-        if (ok) ok = tc_mode<2>(c, S, phase, o, stride_n);
-        if (!ok) {
+        if (__syncthreads_or(bad)) {  // uniform: an MMA wait of the last tile expired somewhere
             failed = true;
             break;
         }
+        float *S = ring + slot * kTcTile;
+        float *o = out + tile_base(t) + (long long)rowm * p.L + colm;
+        if (G == 3) bad |= !tc_mode<0>(c, S, phase, o, stride_n);
+        if (G >= 2) bad |= !tc_mode<1>(c, S, phase, o, stride_n);
+        bad |= !tc_mode<2>(c, S, phase, o, stride_n);
         slot = slot == 2 ? 0 : slot + 1;
     }
+    if (!failed && __syncthreads_or(bad)) failed = true;  // the last tile's vote
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves
     if (failed && tid == 0) atomicExch(tp.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
