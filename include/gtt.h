@@ -150,10 +150,12 @@ gtt_status_t gtt_plan_set_schedule(gtt_plan_t plan, long long max_tile_bytes,
 gtt_status_t gtt_plan_set_passes(gtt_plan_t plan, int count, const int *digits, const long long *runs);
 
 /*
- * gtt_plan_autotune -- time up to max_candidates (<= 0: 64) candidate
- * schedules (mode groups of at most four passes, run lengths, TMA pipeline
- * depth) on scratch buffers of the plan's size, keep the fastest in the plan
- * and record it in the process-wide autotune cache, keyed by GPU name, b, n,
+ * gtt_plan_autotune -- enumerate the candidate schedules (mode groups of at
+ * most four passes, run lengths), rank them by a model of their HBM and FMA
+ * time, and time the max_candidates (<= 0: 64) best-ranked ones in every
+ * pipeline variant (no TMA, TMA with 1..3 buffers) on scratch buffers of the
+ * plan's size; the six fastest are timed again over more runs.  The winner
+ * goes into the plan and into the process-wide autotune cache, keyed by GPU name, b, n,
  * dtype and batch.  Allocates and frees two data-sized device buffers;
  * synchronizes the device.  gtt_plan_create applies a cached schedule when
  * one exists; the environment variable GTT_AUTOTUNE_CACHE names a cache file

@@ -139,7 +139,9 @@ class Plan:
               "gtt_plan_set_passes")
 
     def autotune(self, max_candidates: int = 64):
-        """Time candidate schedules and keep the fastest (recorded in the cache)."""
+        """Time the `max_candidates` best-ranked candidate schedules (ranked by
+        a model of HBM and FMA time), re-time the six fastest, and keep the
+        winner (recorded in the cache)."""
         check(self._lib.gtt_plan_autotune(self._h, int(max_candidates)), "gtt_plan_autotune")
 
     def set_pipeline(self, use_tma: bool = True, nbuf: int = 2):

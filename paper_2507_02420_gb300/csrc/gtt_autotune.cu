@@ -118,7 +118,9 @@ bool tune_apply_cached(gtt_plan_s *P) {
 }
 
 // Candidate schedules: compositions of n into at most 4 passes, with a few
-// run lengths per strided pass, tiles of 2 KiB .. 200 KiB.
+// run lengths per strided pass, tiles of 2 KiB .. 200 KiB (all of them, up to
+// kEnumCap; autotune ranks them with model_cost before timing any).
+constexpr size_t kEnumCap = 20000;
 static void enumerate(const gtt_plan_s *P, int m0, std::vector<int> &g, std::vector<long long> &r,
                       std::vector<std::pair<std::vector<int>, std::vector<long long>>> *out, size_t cap) {
     const int b = P->b, n = P->n, es = P->es;
@@ -170,12 +172,69 @@ static void enumerate(const gtt_plan_s *P, int m0, std::vector<int> &g, std::vec
     }
 }
 
+// Model time of one schedule, used only to rank the candidates before they
+// are timed: every pass moves the vector in and out of HBM once and applies g
+// modes (b FMAs per element and mode, 4b for complex types); a pass costs the
+// larger of the two, raised where its tiles are too big for two CTAs per SM,
+// its rows are shorter than a 32-byte sector (or a 128-byte line), or its
+// tiles are so small that per-tile overhead shows.
+static double model_cost(const gtt_plan_s *P, const std::vector<int> &g, const std::vector<long long> &r) {
+    const double total = (double)P->total, es = (double)P->es;
+    const bool cplx = P->dtype == GTT_C64 || P->dtype == GTT_C128;
+    const bool wide = P->dtype == GTT_F64 || P->dtype == GTT_C128;
+    const double fma_rate = wide ? 0.3e12 : 25e12;  // sustained FMAs per second (rough)
+    const double mem = 2.0 * total * es / 5.8e12;
+    double cost = 0.0;
+    int m0 = 0;
+    for (size_t k = 0; k < g.size(); ++k) {
+        double M = 1.0;
+        for (int i = 0; i < g[k]; ++i) M *= P->b;
+        const double tile = M * (double)r[k] * es;
+        const double comp = total * g[k] * P->b * (cplx ? 4.0 : 1.0) / fma_rate;
+        double t = std::max(mem, comp);
+        if (tile > 110.0 * 1024) t *= 1.6;
+        if (tile < 8192.0) t *= 1.3;
+        if (m0 > 0) {
+            const double row = (double)r[k] * es;
+            if (row < 32.0) t *= 2.0;
+            else if (row < 128.0) t *= 1.15;
+        }
+        cost += t;
+        m0 += g[k];
+    }
+    return cost;
+}
+
+// Time `reps` runs of the plan's current passes after one warm-up (microseconds
+// per run), or a negative value if a run failed.
+static double time_passes(gtt_plan_s *P, void *x, void *y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps) {
+    if (run_passes(P, P->Wf, x, y, s) != GTT_OK) return -1.0;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i)
+        if (run_passes(P, P->Wf, x, y, s) != GTT_OK) return -1.0;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms * 1e3 / reps;
+}
+
+// Two rounds: the max_candidates schedules with the lowest model cost are
+// timed in every pipeline variant (no TMA, TMA with 1..3 buffers) over 3 runs;
+// the best kFinalists (schedule, variant) pairs are then timed again over 10
+// runs each and the fastest of those is kept.
+constexpr int kFinalists = 6;
 gtt_status_t autotune(gtt_plan_s *P, int max_candidates) {
     std::vector<std::pair<std::vector<int>, std::vector<long long>>> cands;
     std::vector<int> g;
     std::vector<long long> r;
-    enumerate(P, 0, g, r, &cands, (size_t)std::max(1, max_candidates));
+    enumerate(P, 0, g, r, &cands, kEnumCap);
     if (cands.empty()) return set_error(GTT_ERR_INTERNAL, "no candidate schedule");
+    std::vector<std::pair<double, size_t>> ranked;
+    for (size_t i = 0; i < cands.size(); ++i) ranked.push_back({model_cost(P, cands[i].first, cands[i].second), i});
+    std::stable_sort(ranked.begin(), ranked.end(),
+                     [](const std::pair<double, size_t> &a, const std::pair<double, size_t> &b) { return a.first < b.first; });
+    if (ranked.size() > (size_t)std::max(1, max_candidates)) ranked.resize((size_t)std::max(1, max_candidates));
     const size_t bytes = (size_t)P->total * P->es;
     void *x = nullptr, *y = nullptr;
     cudaError_t e = cudaMalloc(&x, bytes);
@@ -194,36 +253,44 @@ gtt_status_t autotune(gtt_plan_s *P, int max_candidates) {
     P->timing = false;
     const bool old_tma = P->use_tma;
     const int old_nbuf = P->tma_nbuf;
+    struct Timed {
+        double us;
+        size_t cand;
+        int variant;
+    };
+    std::vector<Timed> timed;
+    auto prepare = [&](size_t ci, int variant) -> bool {
+        P->use_tma = variant > 0;
+        P->tma_nbuf = variant > 0 ? variant : 1;
+        std::vector<PassPlan> passes;
+        const auto &c = cands[ci];
+        if (make_explicit_schedule(P, (int)c.first.size(), c.first.data(), c.second.data(), &passes) != GTT_OK)
+            return false;
+        bool any_tma = false;
+        for (auto &pp : passes) any_tma |= pp.tma.on;
+        if (variant > 0 && !any_tma) return false;
+        P->passes = passes;
+        return true;
+    };
+    for (auto &rk : ranked)
+        for (int variant = 0; variant < 4; ++variant) {
+            if (!prepare(rk.second, variant)) continue;
+            const double us = time_passes(P, x, y, s, e0, e1, 3);
+            if (us >= 0.0) timed.push_back({us, rk.second, variant});
+        }
+    std::sort(timed.begin(), timed.end(), [](const Timed &a, const Timed &b) { return a.us < b.us; });
+    if (timed.size() > (size_t)kFinalists) timed.resize(kFinalists);
     TuneEntry best;
     best.us = 1e30;
-    for (auto &c : cands) {
-        for (int variant = 0; variant < 4; ++variant) {  // no TMA, TMA with 1..3 buffers
-            P->use_tma = variant > 0;
-            P->tma_nbuf = variant > 0 ? variant : 1;
-            std::vector<PassPlan> passes;
-            if (make_explicit_schedule(P, (int)c.first.size(), c.first.data(), c.second.data(), &passes) != GTT_OK)
-                continue;
-            bool any_tma = false;
-            for (auto &pp : passes) any_tma |= pp.tma.on;
-            if (variant > 0 && !any_tma) continue;
-            P->passes = passes;
-            if (run_passes(P, P->Wf, x, y, s) != GTT_OK) continue;  // warm-up
-            const int reps = 3;
-            cudaEventRecord(e0, s);
-            bool ok = true;
-            for (int i = 0; i < reps && ok; ++i) ok = run_passes(P, P->Wf, x, y, s) == GTT_OK;
-            cudaEventRecord(e1, s);
-            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double us = ms * 1e3 / reps;
-            if (us < best.us) {
-                best.us = us;
-                best.g = c.first;
-                best.r = c.second;
-                best.tma = variant > 0;
-                best.nbuf = P->tma_nbuf;
-            }
+    for (const Timed &t : timed) {
+        if (!prepare(t.cand, t.variant)) continue;
+        const double us = time_passes(P, x, y, s, e0, e1, 10);
+        if (us >= 0.0 && us < best.us) {
+            best.us = us;
+            best.g = cands[t.cand].first;
+            best.r = cands[t.cand].second;
+            best.tma = t.variant > 0;
+            best.nbuf = P->tma_nbuf;
         }
     }
     cudaGetLastError();
