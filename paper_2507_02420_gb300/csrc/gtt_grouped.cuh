@@ -71,6 +71,31 @@ template <typename T> __device__ __forceinline__ T ld_cg(const T *p) {
     }
 }
 
+// Ask L2 for one item's input tile (M rows of r elements at stride L) before
+// it is read: a bulk prefetch per 16-byte aligned row (one for a contiguous
+// tile), else one line prefetch per 128-byte line of the row.  The DRAM reads
+// of the whole tile then start at once instead of one per load in turn.  L2
+// is the coherence point, so a prefetch never yields stale data.
+__device__ __forceinline__ void group_prefetch(const unsigned char *in, int es, const PassParams &p, long long t) {
+    const uint32_t tid = threadIdx.x, nth = blockDim.x;
+    const long long hi = t / p.lo_blocks;
+    const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
+    const long long base = hi * p.L * (long long)p.M + (long long)lob * p.r;
+    const bool contig = p.L == (long long)p.r || p.M == 1;
+    const uint32_t rows = contig ? 1u : p.M;
+    const uint32_t row_bytes = (contig ? p.tile_elems : p.r) * (uint32_t)es;
+    for (uint32_t row = tid; row < rows; row += nth) {
+        const unsigned char *a = in + (base + (long long)row * p.L) * es;
+        if ((((uintptr_t)a | row_bytes) & 15u) == 0) {
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(row_bytes) : "memory");
+        } else {
+            const uintptr_t end = (uintptr_t)a + row_bytes;
+            for (uintptr_t l = (uintptr_t)a & ~(uintptr_t)127; l < end; l += 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(l));
+        }
+    }
+}
+
 // One tile of one pass (shared-memory staging as in gtt_pass_kernel).
 template <typename T, int B, int D>
 __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p, long long t, T *s,
@@ -211,6 +236,8 @@ __global__ void __launch_bounds__(kGroupThreads, 4) gtt_grouped_kernel(GroupArgs
         const GroupSeg &sg = a.segs[s_seg];
         const GroupReq &rq = a.reqs[sg.req];
         const GroupPass &gp = rq.pass[sg.pass];
+        group_prefetch(reinterpret_cast<const unsigned char *>(sg.pass == 0 ? rq.x : (const void *)rq.y),
+                       rq.dtype == 1 ? 4 : 8, gp.p, item - sg.first_item);
         // W of this request into shared memory, unless it is already there
         const bool new_w = rq.w_off != s_woff;
         if (new_w) {
