@@ -98,42 +98,49 @@ __device__ __forceinline__ void group_prefetch(const unsigned char *in, int es, 
 
 // One tile of one pass (shared-memory staging as in gtt_pass_kernel).
 template <typename T, int B, int D>
-__device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p, long long t, T *s,
+__device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p, long long t, T *__restrict__ s,
                                         const WMat<T, B> &W) {
     constexpr int RB = cpow(B, D);
     constexpr int CE = Vec16<T>::n;
     const uint32_t tid = threadIdx.x, nth = blockDim.x;
+    // the pass parameters live in global memory, and stores to the tile would
+    // otherwise force the compiler to read them again: read each one once
+    // (the tile is restrict-qualified as well; in and out may be the same)
     const uint32_t tile_elems = p.tile_elems, r = p.r;
+    const long long L = p.L;
+    const int vec_mode = p.vec_mode, nstages = p.nstages;
+    const FastDiv div_r = p.div_r, div_cpr = p.div_cpr;
     const long long hi = t / p.lo_blocks;
     const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
-    const long long base = hi * p.L * (long long)p.M + (long long)lob * r;
-    if (p.vec_mode != 0) {  // 16-byte chunks: contiguous tile (1) or rows of r, r % CE == 0 (2)
-        const uint32_t cpr = p.vec_mode == 1 ? tile_elems / CE : r / CE;
-        const long long rstride = p.vec_mode == 1 ? 0 : p.L;
+    const long long base = hi * L * (long long)p.M + (long long)lob * r;
+    if (vec_mode != 0) {  // 16-byte chunks: contiguous tile (1) or rows of r, r % CE == 0 (2)
+        const uint32_t cpr = vec_mode == 1 ? tile_elems / CE : r / CE;
+        const long long rstride = vec_mode == 1 ? 0 : L;
         for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
-            const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
+            const uint32_t row = vec_mode == 1 ? 0u : div_cpr.div(c), cc = c - row * cpr;
             const int4 raw = __ldcg(reinterpret_cast<const int4 *>(in + base + (long long)row * rstride + cc * CE));
             const T *v = reinterpret_cast<const T *>(&raw);
-            const uint32_t e0 = p.vec_mode == 1 ? c * CE : row * r + cc * CE;
+            const uint32_t e0 = vec_mode == 1 ? c * CE : row * r + cc * CE;
 #pragma unroll
             for (int i = 0; i < CE; ++i) s[spos<RB>(e0 + i)] = v[i];
         }
     } else {
         for (uint32_t e = tid; e < tile_elems; e += nth) {
-            const uint32_t row = p.div_r.div(e), col = e - row * r;
-            s[spos<RB>(e)] = ld_cg(in + base + (long long)row * p.L + col);
+            const uint32_t row = div_r.div(e), col = e - row * r;
+            s[spos<RB>(e)] = ld_cg(in + base + (long long)row * L + col);
         }
     }
     __syncthreads();
     const uint32_t nslots = tile_elems / RB;
-    for (int st = 0; st < p.nstages; ++st) {
+    for (int st = 0; st < nstages; ++st) {
         const uint32_t strideA = p.stage_strideA[st];
         const int mask = p.stage_mask[st];
+        const FastDiv div_ba = p.stage_divBa[st];
         for (uint32_t slot = tid; slot < nslots; slot += nth) {
-            const uint32_t rest = p.div_r.div(slot);
+            const uint32_t rest = div_r.div(slot);
             const uint32_t col = slot - rest * r;
-            const uint32_t high = p.stage_divBa[st].div(rest);
-            const uint32_t low = rest - high * p.stage_divBa[st].d;
+            const uint32_t high = div_ba.div(rest);
+            const uint32_t low = rest - high * div_ba.d;
             const uint32_t e0 = high * (strideA * RB) + low * r + col;
             T v[RB];
 #pragma unroll
@@ -144,12 +151,12 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
         }
         __syncthreads();
     }
-    if (p.vec_mode != 0) {
-        const uint32_t cpr = p.vec_mode == 1 ? tile_elems / CE : r / CE;
-        const long long rstride = p.vec_mode == 1 ? 0 : p.L;
+    if (vec_mode != 0) {
+        const uint32_t cpr = vec_mode == 1 ? tile_elems / CE : r / CE;
+        const long long rstride = vec_mode == 1 ? 0 : L;
         for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
-            const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
-            const uint32_t e0 = p.vec_mode == 1 ? c * CE : row * r + cc * CE;
+            const uint32_t row = vec_mode == 1 ? 0u : div_cpr.div(c), cc = c - row * cpr;
+            const uint32_t e0 = vec_mode == 1 ? c * CE : row * r + cc * CE;
             T v[CE];
 #pragma unroll
             for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(e0 + i)];
@@ -157,8 +164,8 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
         }
     } else {
         for (uint32_t e = tid; e < tile_elems; e += nth) {
-            const uint32_t row = p.div_r.div(e), col = e - row * r;
-            out[base + (long long)row * p.L + col] = s[spos<RB>(e)];
+            const uint32_t row = div_r.div(e), col = e - row * r;
+            out[base + (long long)row * L + col] = s[spos<RB>(e)];
         }
     }
 }
