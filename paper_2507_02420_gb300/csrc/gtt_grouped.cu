@@ -112,6 +112,7 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
         gr.dtype = (int)R.dtype;
         gr.npass = (int)P->passes.size();
         gr.w_off = (int)off;
+        gr.w_bytes = (int)((Wb.size() + 15) / 16 * 16);
         for (int k = 0; k < gr.npass; ++k) {
             gr.pass[k].p = P->passes[k].params;
             gr.pass[k].D = P->passes[k].D;
@@ -141,6 +142,7 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
             sg.req = q;
             sg.pass = p;
             sg.dep = p > 0 ? seg_of[q][p - 1] : -1;
+            sg.dep_tiles = p > 0 ? (unsigned int)hreqs[q].pass[p - 1].p.tiles : 0u;
             sg.first_item = items;
             sg.tiles = hreqs[q].pass[p].p.tiles;
             items += sg.tiles;

@@ -39,12 +39,13 @@ struct GroupReq {
     const void *x;
     void *y;
     int b, dtype, npass, w_off;
+    int w_bytes, pad_;  // size of this request's W in the blob (a multiple of 16)
     GroupPass pass[kGroupMaxPass];
 };
 
 struct GroupSeg {
     int req, pass, dep;  // dep: segment that must complete first, -1 if none
-    int pad_;
+    unsigned int dep_tiles;  // tiles of segment dep (what done[dep] must reach)
     long long first_item, tiles;
 };
 
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kGroupThreads, 4) gtt_grouped_kernel(GroupArgs
                 seg = (int)a.item_seg[item];
                 const int dep = a.segs[seg].dep;
                 if (dep >= 0) {  // bounded wait for the previous pass of this request
-                    const unsigned int need = (unsigned int)a.segs[dep].tiles;
+                    const unsigned int need = a.segs[seg].dep_tiles;
                     uint32_t spins = 0;
                     while (*((volatile unsigned int *)&a.done[dep]) < need) {
                         if (++spins > kGroupSpinLimit) {
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kGroupThreads, 4) gtt_grouped_kernel(GroupArgs
         // W of this request into shared memory, unless it is already there
         const bool new_w = rq.w_off != s_woff;
         if (new_w) {
-            const int wb = a.w_smem_bytes;
+            const int wb = rq.w_bytes;
             const int4 *src = reinterpret_cast<const int4 *>(a.wblob + rq.w_off);
             int4 *dst = reinterpret_cast<int4 *>(smem);
             for (int i = tid; i < wb / 16; i += blockDim.x) dst[i] = src[i];
