@@ -117,6 +117,7 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
     if (vec_mode != 0) {  // 16-byte chunks: contiguous tile (1) or rows of r, r % CE == 0 (2)
         const uint32_t cpr = vec_mode == 1 ? tile_elems / CE : r / CE;
         const long long rstride = vec_mode == 1 ? 0 : L;
+#pragma unroll 4
         for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
             const uint32_t row = vec_mode == 1 ? 0u : div_cpr.div(c), cc = c - row * cpr;
             const int4 raw = __ldcg(reinterpret_cast<const int4 *>(in + base + (long long)row * rstride + cc * CE));
@@ -126,6 +127,7 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
             for (int i = 0; i < CE; ++i) s[spos<RB>(e0 + i)] = v[i];
         }
     } else {
+#pragma unroll 4
         for (uint32_t e = tid; e < tile_elems; e += nth) {
             const uint32_t row = div_r.div(e), col = e - row * r;
             s[spos<RB>(e)] = ld_cg(in + base + (long long)row * L + col);
