@@ -494,6 +494,12 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
     return res
 
 
+def _fma_per_s() -> float:
+    """FP32 FMA peak (FMAs per second): 152 SMs x 128 lanes at the maximum SM clock."""
+    peaks, _ = measured_peaks()
+    return SMS * FP32_LANES * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+
+
 def extra_train(g, dev, hbm, reps=10):
     """b = 8, n = 7, batch 32, FP32 training step: forward + backward (dx, dW)."""
     import torch
@@ -512,7 +518,16 @@ def extra_train(g, dev, hbm, reps=10):
     tc = _time_device(lambda: p3.forward(x3d, out=y3d), reps=reps)
     p3.set_chunking(0)
     tf = _time_device(lambda: p3.forward(x3d, out=y3d), reps=reps)
+    # floor: forward one round trip (x in, y out) plus backward reads of x and dy
+    # and the write of dx; n*b FMAs per element forward, 3*n*b backward
+    # (recompute, adjoint, dW outer products)
+    el = x3d.numel()
+    t_mem = 5 * el * 4 / (hbm * 1e9)
+    t_fma = el * 4 * 7 * 8 / _fma_per_s()
+    floor = max(t_mem, t_fma)
     res = {"ms": t * 1e3, "gelem_s": x3d.numel() / t / 1e9,
+           "roofline": {"floor_ms": floor * 1e3, "frac": floor / t, "bound": "alu" if t_fma > t_mem else "hbm",
+                        "basis": "max(5 x 4 B per element of HBM traffic, 4*n*b FMAs per element at the FP32 peak)"},
            "includes": "gtt_forward + gtt_backward (dx and dW)", "schedule": "autotuned at plan time (untimed)",
            "forward_ms": tf * 1e3, "forward_l2chunked_ms": tc * 1e3}
     del x3d, y3d, dy3, p3
@@ -520,13 +535,18 @@ def extra_train(g, dev, hbm, reps=10):
     return res
 
 
-def extra_grouped(g, dev, hbm, reps=10):
-    """1000 uneven requests in one persistent launch (CUDA graph)."""
+def extra_grouped(g, dev, hbm, reps=10, count=1000):
+    """`count` uneven requests (the first ones of the 1000-request workload) in
+    one persistent launch (CUDA graph)."""
     import torch
     reqs = []
     elems = 0
     nbytes = 0
-    for r in gi.grouped_requests():
+    floor = 0.0  # sum over requests of max(one HBM round trip, n*N*b FMAs (x4 complex) at the FP32 peak)
+    fma = _fma_per_s()
+    for r in gi.grouped_requests()[:count]:
+        es = 8 if r.dtype == "c64" else 4
+        floor += max(2 * r.N * es / (hbm * 1e9), r.n * r.N * r.b * (4 if r.dtype == "c64" else 1) / fma)
         W, x = gi.request_inputs(r)
         xd = torch.from_numpy(x).to(dev)
         reqs.append(dict(b=r.b, n=r.n, dtype=r.dtype, W=W, x=xd, y=torch.empty_like(xd)))
@@ -538,7 +558,9 @@ def extra_grouped(g, dev, hbm, reps=10):
     d = grp.describe()
     return {"ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
             "kernel_launches_per_execute": 1, "work_items": d["work_items"],
-            "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9}
+            "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9,
+            "roofline": {"floor_ms": floor * 1e3, "frac": floor / t,
+                         "basis": "sum over requests of max(one HBM round trip, n*N*b FMAs (x4 complex) at the FP32 peak)"}}
 
 
 def extra_filter(g, dev, hbm, reps=10):
@@ -609,7 +631,7 @@ EXTRAS = {"b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_tra
           "codec": ("b4_n13_c64_topk_codec", extra_codec), "mixed": ("mixed_radix_9_factors_c64", extra_mixed)}
 
 
-def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64):
+def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64, grouped_requests=1000):
     """The other hot-path rows, each timed on its own workload (not part of
     `value`): the b=16 contraction on both paths, the b=8 training step
     (forward + hand-written backward) and the 1000-request grouped launch."""
@@ -617,7 +639,13 @@ def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64):
     out = {}
     for key, (name, fn) in EXTRAS.items():
         if only is None or key == only:
-            out[name] = fn(g, dev, hbm, reps, b16_batch) if key == "b16" else fn(g, dev, hbm, reps)
+            if key == "b16":
+                out[name] = fn(g, dev, hbm, reps, b16_batch)
+            elif key == "grouped":
+                out[name if grouped_requests == 1000 else f"grouped_{grouped_requests}_uneven"] = \
+                    fn(g, dev, hbm, reps, grouped_requests)
+            else:
+                out[name] = fn(g, dev, hbm, reps)
     return out
 
 
@@ -636,6 +664,8 @@ def main():
                          "used for short profiler runs")
     ap.add_argument("--b16-batch", type=int, default=64,
                     help="batch of the b=16 extra (smaller for profiler runs)")
+    ap.add_argument("--grouped-requests", type=int, default=1000,
+                    help="requests of the grouped extra: the first K of the 1000 (smaller for profiler runs)")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the plan's default schedule instead of the autotuned one")
@@ -661,7 +691,7 @@ def main():
         torch.cuda.set_device(dev)
         peaks, _ = measured_peaks()
         print(json.dumps(run_extras(g, dev, peaks, only=args.only, reps=max(1, args.steps),
-                                    b16_batch=args.b16_batch)), flush=True)
+                                    b16_batch=args.b16_batch, grouped_requests=args.grouped_requests)), flush=True)
         return 0
     if world > 1:
         import torch
