@@ -199,24 +199,27 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- GPU arm
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=None) -> str:
+    """Hash of the named csrc files (in the given order), or of every .cu/.cuh/.h
+    file there when `files` is None."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_02420_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    names = files if files is not None else sorted(n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh", ".h")))
+    for name in names:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str):
-    """dram bytes per launch recorded by an ncu capture of this exact kernel
-    source (profiles/traffic.json), else None."""
+    """dram bytes per launch recorded by an ncu capture of this kernel
+    (profiles/traffic.json), while the source files the record names (the
+    kernel and the headers it includes) are unchanged, else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
         ent = rec.get(kernel)
-        if ent and ent.get("source_hash") == kernel_source_hash():
+        if ent and ent.get("source_hash") == kernel_source_hash(ent.get("sources")):
             return ent["dram_bytes_per_launch"]
     except Exception:
         pass
