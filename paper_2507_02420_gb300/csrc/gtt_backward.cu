@@ -54,16 +54,19 @@ gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
     while (m0 < n) {
         long long r = 1;
         const long long L = ipow_ll(b, m0);
-        if (m0 > 0)
-            while (r * b <= L && r * es < 128 &&
-                   bwd_smem_bytes(b, 1, b * r * b, es, cplx) <= smem_budget)
-                r *= b;
         int g = 1;
-        while (m0 + g < n && bwd_smem_bytes(b, g + 1, ipow_ll(b, g + 1) * r, es, cplx) <= smem_budget)
-            ++g;
-        if (m0 > 0 && m0 + g == n)
-            while (r * b <= L && bwd_smem_bytes(b, g, ipow_ll(b, g) * r * b, es, cplx) <= smem_budget)
+        if (m0 == 0) {
+            while (m0 + g < n && bwd_smem_bytes(b, g + 1, ipow_ll(b, g + 1), es, cplx) <= smem_budget) ++g;
+        } else {
+            // fewer passes first: as many modes as fit with runs of at least one
+            // 32-byte sector, then the longest runs (up to a 128-byte line, more
+            // on the last pass) that still fit with those modes
+            while (r * b <= L && r * es < 32) r *= b;
+            while (m0 + g < n && bwd_smem_bytes(b, g + 1, ipow_ll(b, g + 1) * r, es, cplx) <= smem_budget) ++g;
+            while (r * b <= L && (r * es < 128 || m0 + g == n) &&
+                   bwd_smem_bytes(b, g, ipow_ll(b, g) * r * b, es, cplx) <= smem_budget)
                 r *= b;
+        }
         BwdPass bp;
         bp.g = g;
         gtt_status_t st = build_pass(P, m0, g, r, 1, &bp.geo);  // D = 1: one stage per digit
