@@ -126,6 +126,21 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
 #pragma unroll
             for (int i = 0; i < CE; ++i) s[spos<RB>(e0 + i)] = v[i];
         }
+    } else if (L == (long long)r) {
+        // contiguous, but not in whole 16-byte chunks (odd b): the elements up to
+        // the first 16-byte boundary one by one, then chunks, then the rest
+        const T *src = in + base;
+        const uint32_t head = min(tile_elems, (uint32_t)((CE - ((uintptr_t)src / sizeof(T)) % CE) % CE));
+        const uint32_t nch = (tile_elems - head) / CE, mid_end = head + nch * CE;
+        for (uint32_t e = tid; e < head; e += nth) s[spos<RB>(e)] = ld_cg(src + e);
+#pragma unroll 4
+        for (uint32_t c = tid; c < nch; c += nth) {
+            const int4 raw = __ldcg(reinterpret_cast<const int4 *>(src + head + c * CE));
+            const T *v = reinterpret_cast<const T *>(&raw);
+#pragma unroll
+            for (int i = 0; i < CE; ++i) s[spos<RB>(head + c * CE + i)] = v[i];
+        }
+        for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) s[spos<RB>(e)] = ld_cg(src + e);
     } else {
 #pragma unroll 4
         for (uint32_t e = tid; e < tile_elems; e += nth) {
@@ -165,6 +180,18 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
             for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(e0 + i)];
             store16(out + base + (long long)row * rstride + cc * CE, v);
         }
+    } else if (L == (long long)r) {  // contiguous, not in whole chunks: as the load
+        T *dst = out + base;
+        const uint32_t head = min(tile_elems, (uint32_t)((CE - ((uintptr_t)dst / sizeof(T)) % CE) % CE));
+        const uint32_t nch = (tile_elems - head) / CE, mid_end = head + nch * CE;
+        for (uint32_t e = tid; e < head; e += nth) dst[e] = s[spos<RB>(e)];
+        for (uint32_t c = tid; c < nch; c += nth) {
+            T v[CE];
+#pragma unroll
+            for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(head + c * CE + i)];
+            store16(dst + head + c * CE, v);
+        }
+        for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) dst[e] = s[spos<RB>(e)];
     } else {
         for (uint32_t e = tid; e < tile_elems; e += nth) {
             const uint32_t row = div_r.div(e), col = e - row * r;
