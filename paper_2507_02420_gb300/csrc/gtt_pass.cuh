@@ -179,6 +179,20 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
 #pragma unroll
                 for (int i = 0; i < CE; ++i) s[spos<RB>(row * r + cc * CE + i)] = v[i];
             }
+        } else if (p.L == (long long)r) {
+            // contiguous, but not in whole 16-byte chunks (odd radices): the
+            // elements up to the first 16-byte boundary one by one, then
+            // chunks, then the rest
+            const uint32_t head = min(tile_elems, (uint32_t)((CE - ((uintptr_t)gin / sizeof(T)) % CE) % CE));
+            const uint32_t nch = (tile_elems - head) / CE, mid_end = head + nch * CE;
+            for (uint32_t e = tid; e < head; e += nth) s[spos<RB>(e)] = gin[e];
+            for (uint32_t c = tid; c < nch; c += nth) {
+                T v[CE];
+                load16(gin + head + (size_t)c * CE, v);
+#pragma unroll
+                for (int i = 0; i < CE; ++i) s[spos<RB>(head + c * CE + i)] = v[i];
+            }
+            for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) s[spos<RB>(e)] = gin[e];
         } else {
             for (uint32_t e = tid; e < tile_elems; e += nth) {
                 const uint32_t row = p.div_r.div(e), col = e - row * r;
@@ -227,6 +241,17 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
                 for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(row * r + cc * CE + i)];
                 store16(gout + (long long)row * p.L + cc * CE, v);
             }
+        } else if (p.L == (long long)r) {  // contiguous, not in whole chunks: as the load
+            const uint32_t head = min(tile_elems, (uint32_t)((CE - ((uintptr_t)gout / sizeof(T)) % CE) % CE));
+            const uint32_t nch = (tile_elems - head) / CE, mid_end = head + nch * CE;
+            for (uint32_t e = tid; e < head; e += nth) gout[e] = s[spos<RB>(e)];
+            for (uint32_t c = tid; c < nch; c += nth) {
+                T v[CE];
+#pragma unroll
+                for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(head + c * CE + i)];
+                store16(gout + head + (size_t)c * CE, v);
+            }
+            for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) gout[e] = s[spos<RB>(e)];
         } else {
             for (uint32_t e = tid; e < tile_elems; e += nth) {
                 const uint32_t row = p.div_r.div(e), col = e - row * r;
