@@ -15,6 +15,13 @@
 // number (T's lower bits are then zero), at the latest after the last digit.
 // The coefficients with key >= T are collected (exactly k), one CTA per
 // vector sorts them by key descending, and the values are gathered.
+// Before the radix passes, one pass histograms the top 12 bits of the keys and
+// a second pass collects every coefficient whose top bits reach the bucket
+// that holds the k-th largest key: a candidate list that contains all the k
+// largest keys, typically a few times k long.  The radix passes and the final
+// collection then read the candidates instead of the spectrum.  A vector whose
+// candidates exceed the list's capacity (many equal magnitudes) keeps reading
+// its spectrum; the result is the same either way.
 // |c|^2 is formed with explicit round-to-nearest products and sum (no fused
 // multiply-add), so the decision can be reproduced in the same precision.
 #include <algorithm>
@@ -26,6 +33,8 @@ namespace gtt {
 
 constexpr int kTopkMax = 4096;   // k per vector (one CTA sorts them in shared memory)
 constexpr int kTopkSortThreads = 1024;
+constexpr int kTopkBins = 4096;           // buckets of the pre-pass: the top 12 bits of the key
+constexpr uint32_t kTopkCandCap = 65536;  // candidate list capacity per vector
 
 template <typename T> struct KeyOf;
 template <> struct KeyOf<float> {
@@ -55,6 +64,7 @@ struct TopkState {
     uint32_t need;                  // how many keys of the current bucket are still to be taken
     uint32_t done;                  // 1: the threshold T = (key_prefix, idx_prefix) is final
     uint32_t count;                 // keys collected so far
+    uint32_t fast;                  // 1: selected from a short candidate list by one sort
 };
 
 // Digit `pass` of the composite key: the key's KB bits (KB / 8 digits), then
@@ -78,101 +88,223 @@ __device__ __forceinline__ bool digit_of(K key, uint32_t idx, int pass, const To
     return true;
 }
 
+// fn(element, index) over this CTA's share of one vector (grid-stride over
+// blockIdx.x): 16-byte loads when the vector is a whole number of 16-byte
+// chunks (so every vector of the batch starts on a 16-byte boundary), else
+// one element at a time.
+template <typename T, typename F>
+__device__ __forceinline__ void topk_for_each(const T *v, long long N, F fn) {
+    constexpr int CE = 16 / (int)sizeof(T);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (N % CE == 0) {
+        const int4 *v4 = reinterpret_cast<const int4 *>(v);
+        const long long nch = N / CE;
+#pragma unroll 2
+        for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nch; c += stride) {
+            const int4 raw = v4[c];
+            const T *x = reinterpret_cast<const T *>(&raw);
+#pragma unroll
+            for (int i = 0; i < CE; ++i) fn(x[i], c * CE + i);
+        }
+    } else {
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) fn(v[e], e);
+    }
+}
+
+// Pre-pass 1: histogram of the top 12 key bits of vector blockIdx.y.
+template <typename T>
+__global__ void __launch_bounds__(256) gtt_topk_bins_kernel(const T *spec, long long N, uint32_t *bins) {
+    using K = typename KeyOf<T>::K;
+    constexpr int SH = 8 * (int)sizeof(K) - 12;
+    __shared__ uint32_t h[kTopkBins];
+    for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const long long item = blockIdx.y;
+    const T *v = spec + item * N;
+    topk_for_each<T>(v, N, [&](const T &x, long long) { atomicAdd(&h[(uint32_t)(KeyOf<T>::key(x) >> SH)], 1u); });
+    __syncthreads();
+    uint32_t *g = bins + item * kTopkBins;
+    for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&g[i], h[i]);
+}
+
+// The bucket of vector blockIdx.x that holds its k-th largest key (the
+// counts of the buckets from the top reach k there).
+__global__ void __launch_bounds__(256) gtt_topk_binscan_kernel(long long k, const uint32_t *bins, uint32_t *thr) {
+    constexpr int PER = kTopkBins / 256;
+    const long long item = blockIdx.x;
+    const uint32_t *g = bins + item * kTopkBins;
+    __shared__ uint32_t h[kTopkBins];
+    __shared__ uint32_t part[256];
+    for (int i = threadIdx.x; i < kTopkBins; i += 256) h[i] = g[i];
+    __syncthreads();
+    uint32_t sum = 0;
+    for (int i = 0; i < PER; ++i) sum += h[threadIdx.x * PER + i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long above = 0;
+        int chunk = 0;
+        for (int c = 255; c >= 0; --c) {
+            if (above + part[c] >= k) {
+                chunk = c;
+                break;
+            }
+            above += part[c];
+        }
+        int bin = chunk * PER;
+        for (int b = chunk * PER + PER - 1; b >= chunk * PER; --b) {
+            if (above + h[b] >= k) {
+                bin = b;
+                break;
+            }
+            above += h[b];
+        }
+        thr[item] = (uint32_t)bin;
+    }
+}
+
+// Pre-pass 2: the candidates of vector blockIdx.y, every coefficient whose
+// top 12 key bits reach its threshold bucket (cand_n counts them all; at most
+// cap are stored).
+template <typename T>
+__global__ void __launch_bounds__(256) gtt_topk_cand_kernel(const T *spec, long long N, const uint32_t *thr,
+                                                            uint32_t cap, uint32_t *cand_n,
+                                                            typename KeyOf<T>::K *cand_key, uint32_t *cand_idx) {
+    using K = typename KeyOf<T>::K;
+    constexpr int SH = 8 * (int)sizeof(K) - 12;
+    const long long item = blockIdx.y;
+    const uint32_t tb = thr[item];
+    const T *v = spec + item * N;
+    topk_for_each<T>(v, N, [&](const T &x, long long e) {
+        const K key = KeyOf<T>::key(x);
+        if ((uint32_t)(key >> SH) >= tb) {
+            const uint32_t slot = atomicAdd(&cand_n[item], 1u);
+            if (slot < cap) {
+                cand_key[item * cap + slot] = key;
+                cand_idx[item * cap + slot] = (uint32_t)e;
+            }
+        }
+    });
+}
+
 // Histogram of digit `pass` over the matching keys of vector blockIdx.y.
+// The scan of digit `pass` for one vector: pick the digit whose bucket holds
+// the threshold, update the state, clear the histogram.  Run by thread 0.
+template <typename K>
+__device__ void topk_scan_digit(int pass, TopkState *state, uint32_t *h) {
+    constexpr int KB = 8 * (int)sizeof(K), KD = KB / 8;
+    TopkState st = *state;
+    uint32_t above = 0;
+    for (int d = 255; d >= 0; --d) {
+        const uint32_t c = __ldcg(&h[d]);
+        if (above + c >= st.need) {  // the threshold lies in bucket d
+            if (pass < KD)
+                st.key_prefix |= (unsigned long long)d << (KB - 8 * (pass + 1));
+            else
+                st.idx_prefix |= (uint32_t)d << (24 - 8 * (pass - KD));
+            st.need -= above;
+            if (c == st.need) st.done = 1u;  // the whole bucket is taken
+            break;
+        }
+        above += c;
+    }
+    *state = st;
+}
+
+// Histogram of digit `pass` over the matching keys of vector blockIdx.y; the
+// CTA of the vector that finishes last picks the digit (topk_scan_digit) and
+// clears the histogram and its arrival count for the next pass.  The keys
+// come from the vector's candidates when they all fit the list (cand_n <=
+// cap), else from its spectrum.
 template <typename T>
 __global__ void __launch_bounds__(256) gtt_topk_hist_kernel(const T *spec, long long N, int pass,
-                                                            const TopkState *state, uint32_t *hist) {
+                                                            TopkState *state, uint32_t *hist, uint32_t *arrive,
+                                                            uint32_t cap, const uint32_t *cand_n,
+                                                            const typename KeyOf<T>::K *cand_key,
+                                                            const uint32_t *cand_idx) {
     using K = typename KeyOf<T>::K;
     const long long item = blockIdx.y;
     const TopkState st = state[item];
     if (st.done) return;
     __shared__ uint32_t h[256];
+    __shared__ bool last;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const T *v = spec + item * N;
-    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < N; e += (long long)gridDim.x * 256) {
-        uint32_t d;
-        if (digit_of<K>(KeyOf<T>::key(v[e]), (uint32_t)e, pass, st, &d)) atomicAdd(&h[d], 1u);
-    }
-    __syncthreads();
-    if (h[threadIdx.x]) atomicAdd(&hist[item * 256 + threadIdx.x], h[threadIdx.x]);
-}
-
-// Pick the digit of pass `pass` for vector blockIdx.x and clear its histogram.
-template <typename K>
-__global__ void __launch_bounds__(256) gtt_topk_scan_kernel(int pass, TopkState *state, uint32_t *hist) {
-    constexpr int KB = 8 * (int)sizeof(K), KD = KB / 8;
-    const long long item = blockIdx.x;
-    uint32_t *h = hist + item * 256;
-    if (threadIdx.x == 0 && !state[item].done) {
-        TopkState st = state[item];
-        uint32_t above = 0;
-        for (int d = 255; d >= 0; --d) {
-            const uint32_t c = h[d];
-            if (above + c >= st.need) {  // the threshold lies in bucket d
-                if (pass < KD)
-                    st.key_prefix |= (unsigned long long)d << (KB - 8 * (pass + 1));
-                else
-                    st.idx_prefix |= (uint32_t)d << (24 - 8 * (pass - KD));
-                st.need -= above;
-                if (c == st.need) st.done = 1u;  // the whole bucket is taken
-                break;
-            }
-            above += c;
+    const uint32_t nc = cand_n[item];
+    if (nc <= cap) {
+        const K *ck = cand_key + item * cap;
+        const uint32_t *ci = cand_idx + item * cap;
+        for (long long e = blockIdx.x * 256ll + threadIdx.x; e < nc; e += (long long)gridDim.x * 256) {
+            uint32_t d;
+            if (digit_of<K>(ck[e], ci[e], pass, st, &d)) atomicAdd(&h[d], 1u);
         }
-        state[item] = st;
+    } else {
+        const T *v = spec + item * N;
+        for (long long e = blockIdx.x * 256ll + threadIdx.x; e < N; e += (long long)gridDim.x * 256) {
+            uint32_t d;
+            if (digit_of<K>(KeyOf<T>::key(v[e]), (uint32_t)e, pass, st, &d)) atomicAdd(&h[d], 1u);
+        }
     }
     __syncthreads();
-    h[threadIdx.x] = 0;
+    uint32_t *g = hist + item * 256;
+    if (h[threadIdx.x]) atomicAdd(&g[threadIdx.x], h[threadIdx.x]);
+    __threadfence();  // this CTA's counts before its arrival
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&arrive[item], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();  // every CTA's counts are in
+    if (threadIdx.x == 0) {
+        topk_scan_digit<K>(pass, &state[item], g);
+        arrive[item] = 0u;
+    }
+    __syncthreads();
+    g[threadIdx.x] = 0u;
 }
 
 // Collect the keys >= T of vector blockIdx.y (exactly k of them).
 template <typename T>
 __global__ void __launch_bounds__(256) gtt_topk_collect_kernel(const T *spec, long long N, long long k,
                                                                TopkState *state,
-                                                               typename KeyOf<T>::K *sel_key, uint32_t *sel_idx) {
+                                                               typename KeyOf<T>::K *sel_key, uint32_t *sel_idx,
+                                                               uint32_t cap, const uint32_t *cand_n,
+                                                               const typename KeyOf<T>::K *cand_key,
+                                                               const uint32_t *cand_idx) {
     using K = typename KeyOf<T>::K;
     const long long item = blockIdx.y;
+    if (state[item].fast) return;
     const K tk = (K)state[item].key_prefix;
     const uint32_t ti = state[item].idx_prefix;
-    const T *v = spec + item * N;
-    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < N; e += (long long)gridDim.x * 256) {
-        const K key = KeyOf<T>::key(v[e]);
-        if (key > tk || (key == tk && (uint32_t)e >= ti)) {
+    auto take = [&](K key, uint32_t idx) {
+        if (key > tk || (key == tk && idx >= ti)) {
             const uint32_t slot = atomicAdd(&state[item].count, 1u);
             if (slot < (uint32_t)k) {
                 sel_key[item * k + slot] = key;
-                sel_idx[item * k + slot] = (uint32_t)e;
+                sel_idx[item * k + slot] = idx;
             }
         }
+    };
+    const uint32_t nc = cand_n[item];
+    if (nc <= cap) {
+        for (long long e = blockIdx.x * 256ll + threadIdx.x; e < nc; e += (long long)gridDim.x * 256)
+            take(cand_key[item * cap + e], cand_idx[item * cap + e]);
+    } else {
+        const T *v = spec + item * N;
+        for (long long e = blockIdx.x * 256ll + threadIdx.x; e < N; e += (long long)gridDim.x * 256)
+            take(KeyOf<T>::key(v[e]), (uint32_t)e);
     }
 }
 
-// Sort the k collected (key, index) pairs of vector blockIdx.x by key
-// descending (bitonic, padded to a power of two with entries that sort last;
-// when P2 == size the last merge runs in output order over the whole array)
-// and write the indices and the gathered values.
-template <typename T>
-__global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_sort_kernel(const T *spec, long long N, long long k,
-                                                                         const typename KeyOf<T>::K *sel_key,
-                                                                         const uint32_t *sel_idx, long long *out_idx,
-                                                                         T *out_val) {
-    using K = typename KeyOf<T>::K;
-    constexpr uint32_t kPad = 0xFFFFFFFFu;  // index of a padding entry (real indices are < 2^32 - 1)
-    __shared__ K sk[kTopkMax];
-    __shared__ uint32_t si[kTopkMax];
-    const long long item = blockIdx.x;
-    int P2 = 1;
-    while (P2 < k) P2 <<= 1;
-    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
-        const bool ok = i < k;
-        sk[i] = ok ? sel_key[item * k + i] : (K)0;
-        si[i] = ok ? sel_idx[item * k + i] : kPad;
-    }
-    __syncthreads();
-    // "a before b" in the output order: collected pairs first, then key, then index, descending
+// Bitonic sort of the P2 (a power of two) pairs (sk, si) in shared memory
+// into output order: entries with a real index first, then key descending,
+// then index descending (padding entries carry index kTopkPad).  When P2 equals
+// the size of the last merge, that merge runs in output order over the whole
+// array.
+constexpr uint32_t kTopkPad = 0xFFFFFFFFu;  // index of a padding entry (real indices are < 2^32 - 1)
+template <typename K> __device__ void topk_bitonic(K *sk, uint32_t *si, int P2) {
     auto before = [&](int a, int b) {
-        const bool va = si[a] != kPad, vb = si[b] != kPad;
+        const bool va = si[a] != kTopkPad, vb = si[b] != kTopkPad;
         if (va != vb) return va;
         if (sk[a] != sk[b]) return sk[a] > sk[b];
         return si[a] > si[b];
@@ -196,9 +328,67 @@ __global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_sort_kernel(const T
             __syncthreads();
         }
     }
+}
+
+// Sort the k collected (key, index) pairs of vector blockIdx.x and write the
+// indices and the gathered values (vectors selected by the fast sort are done).
+template <typename T>
+__global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_sort_kernel(const T *spec, long long N, long long k,
+                                                                         const typename KeyOf<T>::K *sel_key,
+                                                                         const uint32_t *sel_idx, long long *out_idx,
+                                                                         T *out_val, const TopkState *state) {
+    using K = typename KeyOf<T>::K;
+    __shared__ K sk[kTopkMax];
+    __shared__ uint32_t si[kTopkMax];
+    const long long item = blockIdx.x;
+    if (state[item].fast) return;
+    int P2 = 1;
+    while (P2 < k) P2 <<= 1;
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        const bool ok = i < k;
+        sk[i] = ok ? sel_key[item * k + i] : (K)0;
+        si[i] = ok ? sel_idx[item * k + i] : kTopkPad;
+    }
+    __syncthreads();
+    topk_bitonic<K>(sk, si, P2);
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         out_idx[item * k + i] = (long long)si[i];
         out_val[item * k + i] = spec[item * N + si[i]];
+    }
+}
+
+// A vector whose candidate list holds at most kTopkMax entries: sort the whole
+// list in one CTA, write its first k entries and mark the vector done, so the
+// radix passes, the collection and the sort above pass it by.
+template <typename T>
+__global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_fastsort_kernel(const T *spec, long long N, long long k,
+                                                                             uint32_t cap, const uint32_t *cand_n,
+                                                                             const typename KeyOf<T>::K *cand_key,
+                                                                             const uint32_t *cand_idx,
+                                                                             long long *out_idx, T *out_val,
+                                                                             TopkState *state) {
+    using K = typename KeyOf<T>::K;
+    __shared__ K sk[kTopkMax];
+    __shared__ uint32_t si[kTopkMax];
+    const long long item = blockIdx.x;
+    const uint32_t nc = cand_n[item];
+    if (nc > cap || nc > (uint32_t)kTopkMax) return;  // the radix passes select this vector
+    int P2 = 1;
+    while (P2 < (int)nc) P2 <<= 1;
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        const bool ok = i < (int)nc;
+        sk[i] = ok ? cand_key[item * cap + i] : (K)0;
+        si[i] = ok ? cand_idx[item * cap + i] : kTopkPad;
+    }
+    __syncthreads();
+    topk_bitonic<K>(sk, si, P2);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        out_idx[item * k + i] = (long long)si[i];
+        out_val[item * k + i] = spec[item * N + si[i]];
+    }
+    if (threadIdx.x == 0) {
+        state[item].done = 1u;
+        state[item].fast = 1u;
     }
 }
 
@@ -214,10 +404,12 @@ __global__ void __launch_bounds__(256) gtt_topk_scatter_kernel(const long long *
 }
 
 template <typename T> struct TopkKernels {
+    static const void *bins() { return (const void *)&gtt_topk_bins_kernel<T>; }
+    static const void *cand() { return (const void *)&gtt_topk_cand_kernel<T>; }
     static const void *hist() { return (const void *)&gtt_topk_hist_kernel<T>; }
-    static const void *scan() { return (const void *)&gtt_topk_scan_kernel<typename KeyOf<T>::K>; }
     static const void *collect() { return (const void *)&gtt_topk_collect_kernel<T>; }
     static const void *sort() { return (const void *)&gtt_topk_sort_kernel<T>; }
+    static const void *fastsort() { return (const void *)&gtt_topk_fastsort_kernel<T>; }
     static const void *scatter() { return (const void *)&gtt_topk_scatter_kernel<T>; }
     static constexpr int key_bytes = (int)sizeof(typename KeyOf<T>::K);
 };
@@ -228,11 +420,26 @@ static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, lo
     using TK = TopkKernels<T>;
     const long long B = P->batch, N = P->N;
     const int KB = TK::key_bytes;
-    // workspace: states, histograms, collected keys and indices
-    const size_t st_bytes = ((size_t)B * sizeof(TopkState) + 255) / 256 * 256;
-    const size_t h_bytes = (size_t)B * 256 * sizeof(uint32_t);
-    const size_t key_bytes = ((size_t)B * k * KB + 255) / 256 * 256;
-    const size_t need = st_bytes + h_bytes + key_bytes + (size_t)B * k * sizeof(uint32_t);
+    // the candidate pre-passes pay off on long vectors; shorter ones run the
+    // radix passes on the spectrum directly
+    const bool use_cand = N >= 16ll * kTopkCandCap;
+    const uint32_t cap = use_cand ? kTopkCandCap : 0u;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    // workspace: states, radix histograms, collected keys and indices, candidate
+    // counts; with the pre-passes also bucket counts, thresholds and the lists
+    const size_t st_bytes = al((size_t)B * sizeof(TopkState));
+    const size_t h_bytes = al((size_t)B * 256 * sizeof(uint32_t));
+    const size_t key_bytes = al((size_t)B * k * KB);
+    const size_t sidx_bytes = al((size_t)B * k * sizeof(uint32_t));
+    const size_t cn_bytes = al((size_t)B * sizeof(uint32_t));
+    const size_t ar_bytes = al((size_t)B * sizeof(uint32_t));
+    const size_t bins_bytes = use_cand ? al((size_t)B * kTopkBins * sizeof(uint32_t)) : 0;
+    const size_t thr_bytes = use_cand ? al((size_t)B * sizeof(uint32_t)) : 0;
+    const size_t ckey_bytes = use_cand ? al((size_t)B * cap * KB) : 0;
+    const size_t cidx_bytes = use_cand ? al((size_t)B * cap * sizeof(uint32_t)) : 0;
+    const size_t need =
+        st_bytes + h_bytes + key_bytes + sidx_bytes + cn_bytes + ar_bytes + bins_bytes + thr_bytes + ckey_bytes +
+        cidx_bytes;
     if (P->ws_topk_bytes < need) {
         if (P->ws_topk) cudaFree(P->ws_topk);
         P->ws_topk = nullptr;
@@ -246,39 +453,75 @@ static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, lo
     }
     unsigned char *w = static_cast<unsigned char *>(P->ws_topk);
     TopkState *state = reinterpret_cast<TopkState *>(w);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(w + st_bytes);
-    void *sel_key = w + st_bytes + h_bytes;
-    uint32_t *sel_idx = reinterpret_cast<uint32_t *>(w + st_bytes + h_bytes + key_bytes);
-    // initial state: nothing chosen, k needed
+    w += st_bytes;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w);
+    w += h_bytes;
+    void *sel_key = w;
+    w += key_bytes;
+    uint32_t *sel_idx = reinterpret_cast<uint32_t *>(w);
+    w += sidx_bytes;
+    uint32_t *cand_n = reinterpret_cast<uint32_t *>(w);
+    w += cn_bytes;
+    uint32_t *arrive = reinterpret_cast<uint32_t *>(w);  // CTAs of a vector done with the current digit
+    w += ar_bytes;
+    uint32_t *bins = reinterpret_cast<uint32_t *>(w);
+    w += bins_bytes;
+    uint32_t *thr = reinterpret_cast<uint32_t *>(w);
+    w += thr_bytes;
+    void *cand_key = w;
+    w += ckey_bytes;
+    uint32_t *cand_idx = reinterpret_cast<uint32_t *>(w);
+    // initial state: nothing chosen, k needed; no candidates (a count above
+    // cap sends every pass to the spectrum)
     std::vector<TopkState> init((size_t)B);
-    for (TopkState &t : init) t = TopkState{0ull, 0u, (uint32_t)k, 0u, 0u};
+    for (TopkState &t : init) t = TopkState{0ull, 0u, (uint32_t)k, 0u, 0u, 0u};
     cudaError_t e = cudaMemcpyAsync(state, init.data(), (size_t)B * sizeof(TopkState), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, h_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(arrive, 0, ar_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cand_n, use_cand ? 0 : 0xFF, (size_t)B * sizeof(uint32_t), s);
+    if (e == cudaSuccess && use_cand) e = cudaMemsetAsync(bins, 0, bins_bytes, s);
     if (e != cudaSuccess) return cuda_error(e, "top-k workspace set-up");
     // pass geometry: blocks per vector so the whole batch fills the GPU
     const long long per_item = std::max<long long>(1, std::min<long long>((N + 2047) / 2048,
                                                                            (8ll * P->num_sms + B - 1) / B));
     const dim3 grid((unsigned)per_item, (unsigned)B);
-    const int passes = KB + 4;  // key digits, then index digits
-    gtt_status_t st;
-    for (int pass = 0; pass < passes; ++pass) {
-        const void *sp = spec;
-        long long n = N;
-        int ps = pass;
-        void *hargs[5] = {(void *)&sp, (void *)&n, (void *)&ps, (void *)&state, (void *)&hist};
-        st = launch_timed(P, TK::hist(), grid, dim3(256), hargs, 0, s, "gtt_topk_hist_kernel");
-        if (st != GTT_OK) return st;
-        void *sargs[3] = {(void *)&ps, (void *)&state, (void *)&hist};
-        st = launch_timed(P, TK::scan(), dim3((unsigned)B), dim3(256), sargs, 0, s, "gtt_topk_scan_kernel");
-        if (st != GTT_OK) return st;
-    }
     const void *sp = spec;
     long long n = N, kk = k;
-    void *cargs[6] = {(void *)&sp, (void *)&n, (void *)&kk, (void *)&state, (void *)&sel_key, (void *)&sel_idx};
+    uint32_t cp = cap;
+    gtt_status_t st;
+    if (use_cand) {
+        void *bargs[3] = {(void *)&sp, (void *)&n, (void *)&bins};
+        st = launch_timed(P, TK::bins(), grid, dim3(256), bargs, 0, s, "gtt_topk_bins_kernel");
+        if (st != GTT_OK) return st;
+        void *targs[3] = {(void *)&kk, (void *)&bins, (void *)&thr};
+        st = launch_timed(P, (const void *)&gtt_topk_binscan_kernel, dim3((unsigned)B), dim3(256), targs, 0, s,
+                          "gtt_topk_binscan_kernel");
+        if (st != GTT_OK) return st;
+        void *cargs[7] = {(void *)&sp, (void *)&n, (void *)&thr, (void *)&cp, (void *)&cand_n, (void *)&cand_key,
+                          (void *)&cand_idx};
+        st = launch_timed(P, TK::cand(), grid, dim3(256), cargs, 0, s, "gtt_topk_cand_kernel");
+        if (st != GTT_OK) return st;
+        void *fargs[10] = {(void *)&sp,       (void *)&n,        (void *)&kk,      (void *)&cp,
+                           (void *)&cand_n,   (void *)&cand_key, (void *)&cand_idx, (void *)&out_idx,
+                           (void *)&out_val,  (void *)&state};
+        st = launch_timed(P, TK::fastsort(), dim3((unsigned)B), dim3(kTopkSortThreads), fargs, 0, s,
+                          "gtt_topk_fastsort_kernel");
+        if (st != GTT_OK) return st;
+    }
+    const int passes = KB + 4;  // key digits, then index digits
+    for (int pass = 0; pass < passes; ++pass) {
+        int ps = pass;
+        void *hargs[10] = {(void *)&sp, (void *)&n,      (void *)&ps,       (void *)&state,   (void *)&hist,
+                           (void *)&arrive, (void *)&cp, (void *)&cand_n, (void *)&cand_key, (void *)&cand_idx};
+        st = launch_timed(P, TK::hist(), grid, dim3(256), hargs, 0, s, "gtt_topk_hist_kernel");
+        if (st != GTT_OK) return st;
+    }
+    void *cargs[10] = {(void *)&sp,      (void *)&n,  (void *)&kk,     (void *)&state,    (void *)&sel_key,
+                       (void *)&sel_idx, (void *)&cp, (void *)&cand_n, (void *)&cand_key, (void *)&cand_idx};
     st = launch_timed(P, TK::collect(), grid, dim3(256), cargs, 0, s, "gtt_topk_collect_kernel");
     if (st != GTT_OK) return st;
-    void *oargs[7] = {(void *)&sp, (void *)&n, (void *)&kk, (void *)&sel_key, (void *)&sel_idx, (void *)&out_idx,
-                      (void *)&out_val};
+    void *oargs[8] = {(void *)&sp,      (void *)&n,       (void *)&kk,      (void *)&sel_key,
+                      (void *)&sel_idx, (void *)&out_idx, (void *)&out_val, (void *)&state};
     return launch_timed(P, TK::sort(), dim3((unsigned)B), dim3(kTopkSortThreads), oargs, 0, s, "gtt_topk_sort_kernel");
 }
 

@@ -122,6 +122,36 @@ def test_all_ties_keep_the_largest_indices(g):
     np.testing.assert_array_equal(idx.cpu().numpy(), np.stack([want, want]))
 
 
+@pytest.mark.parametrize("b,n,dt,batch,k", [(4, 10, "c64", 3, 4096), (2, 21, "f32", 2, 700), (8, 7, "f64", 2, 33)])
+def test_candidate_prepass_selection_is_exact(g, b, n, dt, batch, k):
+    """Vectors of 2^20 elements or more go through the 12-bit bucket pre-pass
+    and a candidate list; the selection must still equal the host's."""
+    rng = np.random.default_rng(9930 + b + n)
+    W, x = make(b, n, batch, dt, rng)
+    plan = g.Plan(W, n, dt, batch)
+    spec_d = torch.empty(batch, b ** n, dtype=plan.torch_dtype, device="cuda")
+    idx, val = plan.compress(torch.from_numpy(x).cuda(), k, spectrum=spec_d)
+    spec = spec_d.cpu().numpy()
+    np.testing.assert_array_equal(idx.cpu().numpy(), host_select(spec, k))
+    np.testing.assert_array_equal(val.cpu().numpy(), np.take_along_axis(spec, idx.cpu().numpy(), axis=1))
+    plan.check()
+
+
+def test_candidate_overflow_falls_back_to_the_spectrum(g):
+    """2^20 equal magnitudes: every coefficient lands in one bucket, the
+    candidate list overflows, and the selection reads the spectrum: the
+    largest indices, in descending order."""
+    W = gi.hadamard_w(True).astype(np.float32)
+    n = 20
+    x = np.zeros((2, 2 ** n), np.float32)
+    x[0, 0] = 1.0
+    x[1, 12345] = 1.0
+    plan = g.Plan(W, n, "f32", 2)
+    idx, _ = plan.compress(torch.from_numpy(x).cuda(), 100)
+    want = np.arange(2 ** n - 1, 2 ** n - 101, -1)
+    np.testing.assert_array_equal(idx.cpu().numpy(), np.stack([want, want]))
+
+
 def test_keeping_everything_reconstructs_x(g):
     rng = np.random.default_rng(9910)
     W, x = make(4, 5, 2, "c64", rng)   # N = 1024 <= 4096
