@@ -32,7 +32,7 @@ struct gtt_group_s {
 
 namespace {
 
-constexpr int kGroupLag = 3;  // pass p of request q follows pass p-1 of request q + lag
+constexpr int kGroupLag = 16;  // pass p of request q follows pass p-1 of request q + lag
 
 gtt_status_t fail(gtt_group_s *G, gtt_status_t st) {
     if (G) {
