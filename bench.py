@@ -161,7 +161,7 @@ def run_reference(args, rank):
     if rank != 0:
         return 0
     import oracle
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     threads = os.cpu_count() or 1
     Wc = W.astype(np.complex128)
     WH = np.ascontiguousarray(Wc.conj().T)
@@ -305,7 +305,7 @@ def run_gpu(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     # plan step: the autotuner times candidate schedules (pass digits, run
     # lengths, pipeline depth) on this GPU and keeps the fastest; with
     # --tune-cache an earlier result is reused (a plan applies cached entries
@@ -463,7 +463,7 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
     each with and without L2 chunking; errors against the FP64 GPU path.
     (`batch` may shrink the batch for short profiler runs.)"""
     import torch
-    W2, x2 = gi.config_inputs(2, batch=batch)
+    W2, x2 = gi.workload_inputs("b16_n6_batch64_f32", batch=batch)
     x2d = torch.from_numpy(x2).to(dev)
     del x2
     n2 = x2d.numel()
@@ -506,12 +506,12 @@ def _fma_per_s() -> float:
 def extra_train(g, dev, hbm, reps=10):
     """b = 8, n = 7, batch 32, FP32 training step: forward + backward (dx, dW)."""
     import torch
-    W3, x3 = gi.config_inputs(3)
+    W3, x3 = gi.workload_inputs("b8_n7_batch32_f32")
     p3 = g.Plan(W3, 7, "f32", 32)
     p3.autotune(64)  # plan step, untimed, as for the main workload
     x3d = torch.from_numpy(x3).to(dev)
     y3d = torch.empty_like(x3d)
-    dy3 = torch.from_numpy(gi.config3_mask()).to(dev) * 2.0
+    dy3 = torch.from_numpy(gi.train_mask()).to(dev) * 2.0
 
     def train_step():
         p3.forward(x3d, out=y3d)
@@ -571,7 +571,7 @@ def extra_filter(g, dev, hbm, reps=10):
     complex64, cut N / 2: forward passes, write-only zeroing of the masked
     half, adjoint passes; against forward + inverse on the same plan."""
     import torch
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     plan = g.Plan(W, NDIG, "c64", BATCH)
     plan.autotune(64)  # plan step, untimed, as for the main workload
     xd = torch.from_numpy(x).to(dev)
@@ -592,7 +592,7 @@ def extra_codec(g, dev, hbm, reps=10, k=1024):
     (radix select where the candidates overflow), and zero + scatter +
     adjoint."""
     import torch
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     plan = g.Plan(W, NDIG, "c64", BATCH)
     plan.autotune(64)  # plan step, untimed, as for the main workload
     xd = torch.from_numpy(x).to(dev)

@@ -7,15 +7,15 @@ sharing any code with each other.
 
 Workloads (all synthetic; the paper uses no public dataset):
 
-* ``cfg0`` -- b=2, n=12, batch 1, FP64; W = [[1,1],[1,-1]]/sqrt(2) (the
+* ``b2_n12_f64`` -- b=2, n=12, batch 1, FP64; W = [[1,1],[1,-1]]/sqrt(2) (the
   normalised Hadamard base matrix of Sec. 2.3, b=2 case), x ~ U[-1, 1].
-* ``cfg1`` -- b=4, n=13, batch 1, complex64; W Haar-random 4x4 unitary,
+* ``b4_n13_c64`` -- b=4, n=13, batch 1, complex64; W Haar-random 4x4 unitary,
   x ~ CN(0, 1) (re, im ~ N(0, 1/2)).
-* ``cfg2`` -- b=16, n=6, batch 64, FP32; W Haar-random 16x16 orthogonal,
+* ``b16_n6_batch64_f32`` -- b=16, n=6, batch 64, FP32; W Haar-random 16x16 orthogonal,
   x ~ N(0, 1).
-* ``cfg3`` -- b=8, n=7, batch 32, FP32; W Haar-random 8x8 orthogonal
+* ``b8_n7_batch32_f32`` -- b=8, n=7, batch 32, FP32; W Haar-random 8x8 orthogonal
   (trainable), x ~ N(0, 1), mask m ~ U[0, 1] with y's shape.
-* ``cfg4`` -- 1000 requests, b uniform on {2,3,4,5,8,16}, N log-uniform in
+* ``grouped_1000_uneven`` -- 1000 requests, b uniform on {2,3,4,5,8,16}, N log-uniform in
   [2^10, 2^22], dtype 50/50 FP32 / complex64, W Haar per request.
 
 Random numbers come from numpy's PCG64 (``numpy.random.default_rng(seed)``).
@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "haar_unitary", "haar_orthogonal", "hadamard_w", "u3",
     "uniform_x", "normal_x", "complex_normal_x", "uniform_mask",
-    "Request", "grouped_requests", "CONFIGS",
+    "Request", "grouped_requests", "WORKLOADS", "workload_inputs", "train_mask",
 ]
 
 
@@ -146,41 +146,44 @@ def request_inputs(req: Request):
     return w, x
 
 
-CONFIGS = {
-    0: dict(name="b2_n12_f64", b=2, n=12, batch=1, dtype="f64", seed=0),
-    1: dict(name="b4_n13_c64", b=4, n=13, batch=1, dtype="c64", seed=1),
-    2: dict(name="b16_n6_batch64_f32", b=16, n=6, batch=64, dtype="f32", seed=2),
-    3: dict(name="b8_n7_batch32_f32_train", b=8, n=7, batch=32, dtype="f32", seed=3),
-    4: dict(name="grouped_1000_uneven", seed=4, count=1000),
+WORKLOADS = {
+    "b2_n12_f64": dict(b=2, n=12, batch=1, dtype="f64", seed=0),
+    "b4_n13_c64": dict(b=4, n=13, batch=1, dtype="c64", seed=1),
+    "b16_n6_batch64_f32": dict(b=16, n=6, batch=64, dtype="f32", seed=2),
+    "b8_n7_batch32_f32": dict(b=8, n=7, batch=32, dtype="f32", seed=3),
+    "grouped_1000_uneven": dict(seed=4, count=1000),
 }
 
 
-def config_inputs(i: int, batch: int | None = None):
-    """(W, x) for configs 0-3 (x has shape [batch, N]).  `batch` may shrink the
-    batch for a sampled run; the first items are identical to the full run's."""
-    c = CONFIGS[i]
+def workload_inputs(name: str, batch: int | None = None):
+    """(W, x) of a single-transform workload (x has shape [batch, N]).  `batch`
+    may shrink the batch for a sampled run; the first items are identical to
+    the full run's."""
+    c = WORKLOADS[name]
+    if "b" not in c:
+        raise ValueError(f"{name} is a request list; use grouped_requests()")
     rng = np.random.default_rng(c["seed"])
     bsz = c["batch"] if batch is None else batch
     N = c["b"] ** c["n"]
-    if i == 0:
+    if name == "b2_n12_f64":
         w = hadamard_w(True)
         x = uniform_x((bsz, N), rng, dtype=np.float64)
-    elif i == 1:
+    elif name == "b4_n13_c64":
         w = haar_unitary(4, rng).astype(np.complex64)
         x = complex_normal_x((bsz, N), rng, np.complex64)
-    elif i == 2:
+    elif name == "b16_n6_batch64_f32":
         w = haar_orthogonal(16, rng).astype(np.float32)
         x = normal_x((bsz, N), rng, np.float32)
-    elif i == 3:
+    else:  # b8_n7_batch32_f32
         w = haar_orthogonal(8, rng).astype(np.float32)
         x = normal_x((bsz, N), rng, np.float32)
-    else:
-        raise ValueError("config 4 is a request list; use grouped_requests()")
     return w, x
 
 
-def config3_mask(batch: int | None = None):
-    c = CONFIGS[3]
+def train_mask(batch: int | None = None):
+    """The loss mask m ~ U[0, 1] of the b8_n7_batch32_f32 training step (its own
+    stream, seeded from the workload's seed)."""
+    c = WORKLOADS["b8_n7_batch32_f32"]
     rng = np.random.default_rng(c["seed"] + 1000)
     bsz = c["batch"] if batch is None else batch
     return uniform_mask((bsz, c["b"] ** c["n"]), rng)

@@ -81,8 +81,8 @@ def test_backward_matches_oracle_gradient(g, dt, b):
 def test_b8_n7_batch32_training_step_full_size(g):
     """b=8, n=7, batch 32, FP32, trainable W (Haar-orthogonal init), loss
     sum(m * y^2): dx (rel-L2 <= 1e-5) and dW (Frobenius <= 1e-4) vs the oracle."""
-    W, x = gi.config_inputs(3)
-    m = gi.config3_mask()
+    W, x = gi.workload_inputs("b8_n7_batch32_f32")
+    m = gi.train_mask()
     Wt = torch.from_numpy(W).cuda().requires_grad_(True)
     xt = torch.from_numpy(x).cuda().requires_grad_(True)
     mt = torch.from_numpy(m).cuda()

@@ -61,7 +61,7 @@ def test_chunked_passes_are_bitwise_identical(g, b, n, batch, dt, prec, tma, chu
 
 
 def test_automatic_chunking_choice(g):
-    W, _ = gi.config_inputs(2)
+    W, _ = gi.workload_inputs("b16_n6_batch64_f32")
     plan = g.Plan(W, 6, "f32", 64)
     plan.set_chunking(-1)   # 4 GiB: 48 MiB chunks of the first two passes
     small = g.Plan(W, 4, "f32", 2)

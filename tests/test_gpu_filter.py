@@ -103,7 +103,7 @@ def test_filter_rejects_bad_cut(g):
 
 def test_filter_full_size_bandwidth_workload(g):
     """b = 4, n = 13, complex64: low-pass at N / 3 against the oracle's filter."""
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     N = 4 ** 13
     plan = g.Plan(W, 13, "c64", 1)
     y = plan.filter(torch.from_numpy(x).cuda(), N // 3, True).cpu().numpy()

@@ -62,7 +62,7 @@ def test_bf16x3_non_orthogonal_w_and_inverse_is_adjoint(g):
 def test_b16_n6_batch64_bf16x3_full_size_sampled(g):
     """b=16, n=6, batch 64: BF16x3 tensor-core path, items 0, 21, 42, 63 vs the
     oracle at rel-L2 <= 1e-6; the FP32 CUDA-core path on the same input too."""
-    W, x = gi.config_inputs(2)
+    W, x = gi.workload_inputs("b16_n6_batch64_f32")
     plan = g.Plan(W, 6, "f32", 64)
     plan.set_precision(g.PREC_BF16X3)
     xd = torch.from_numpy(x).cuda()

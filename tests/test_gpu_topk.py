@@ -178,7 +178,7 @@ def test_codec_rejects_bad_arguments(g):
 
 def test_full_size_bandwidth_workload(g):
     """b = 4, n = 13, complex64, k = 1024: exact selection from the GPU spectrum."""
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     plan = g.Plan(W, 13, "c64", 1)
     spec_d = torch.empty(1, 4 ** 13, dtype=torch.complex64, device="cuda")
     idx, val = plan.compress(torch.from_numpy(x).cuda(), 1024, spectrum=spec_d)

@@ -106,7 +106,7 @@ def test_schedule_sweep(g, sched, b, n, dt):
 def test_b2_n12_f64_against_dense_oracle(g):
     """b=2, n=12, FP64, W = H/sqrt(2): forward and inverse vs the naive O(N^2)
     dense oracle, rel-L2 <= 1e-13."""
-    W, x = gi.config_inputs(0)
+    W, x = gi.workload_inputs("b2_n12_f64")
     y, xr, _ = gpu_fwd_inv(g, W, x, 12, "f64")
     ref = oracle.dense(W, x[0]).real
     assert rel_l2(y[0], ref) <= 1e-13
@@ -118,7 +118,7 @@ def test_b4_n13_c64_full_size(g):
     """b=4, n=13 (N = 2^26), complex64, Haar W, in the default launch
     configuration: forward rel-L2 <= 1e-5, inverse(forward) vs x <= 2e-5,
     norm preserved."""
-    W, x = gi.config_inputs(1)
+    W, x = gi.workload_inputs("b4_n13_c64")
     y, xr, plan = gpu_fwd_inv(g, W, x, 13, "c64")
     ref = oracle.modes(up(W), up(x))
     e = rel_l2(y, ref)
@@ -131,7 +131,7 @@ def test_b4_n13_c64_full_size(g):
 def test_b16_n6_batch64_f32_full_size_sampled(g):
     """b=16, n=6, batch 64, FP32 CUDA-core path: the whole batch runs on the
     GPU; items 0, 21, 42, 63 are checked against the oracle (rel-L2 <= 1e-6)."""
-    W, x = gi.config_inputs(2)
+    W, x = gi.workload_inputs("b16_n6_batch64_f32")
     plan = g.Plan(W, 6, "f32", 64)
     plan.set_precision(g.PREC_FP32)
     xd = torch.from_numpy(x).cuda()
@@ -145,7 +145,7 @@ def test_b16_n6_batch64_f32_full_size_sampled(g):
 
 def test_b8_n7_batch32_f32_forward_sampled(g):
     """b=8, n=7, batch 32, FP32: forward rel-L2 <= 1e-5 on sampled items."""
-    W, x = gi.config_inputs(3)
+    W, x = gi.workload_inputs("b8_n7_batch32_f32")
     plan = g.Plan(W, 7, "f32", 32)
     y = plan.forward(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
