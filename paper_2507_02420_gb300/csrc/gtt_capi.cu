@@ -4,6 +4,7 @@
 // of passes, each applying a contiguous group of modes of Algorithm 1 in one
 // HBM round trip -- and the launch geometry of every pass.
 #include <algorithm>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -244,8 +245,75 @@ static void make_w_params(int dtype, int es, int b, const void *W, std::vector<u
     append_packed_pairs(dtype, b, Wa);
 }
 
+// Kronecker product W_lo (x) W_lo+1 (x) ... (x) W_hi of adjacent factors, in
+// the element layout of `dtype` (row-major).  Formed in double (complex
+// double) and rounded once; int32 entries multiply modulo 2^32.
+static std::vector<unsigned char> kron_factors(int dtype, int es, const std::vector<int> &radices,
+                                               const std::vector<size_t> &off, const unsigned char *W, int lo,
+                                               int hi) {
+    const bool integer = dtype == GTT_I32;
+    auto entry = [&](int k, int i) -> std::complex<double> {
+        const unsigned char *p = W + off[k] + (size_t)i * es;
+        switch (dtype) {
+        case GTT_F64: return *reinterpret_cast<const double *>(p);
+        case GTT_F32: return *reinterpret_cast<const float *>(p);
+        case GTT_C64: return {reinterpret_cast<const float *>(p)[0], reinterpret_cast<const float *>(p)[1]};
+        case GTT_C128: return {reinterpret_cast<const double *>(p)[0], reinterpret_cast<const double *>(p)[1]};
+        default: return 0.0;
+        }
+    };
+    int m = radices[lo];
+    std::vector<std::complex<double>> M((size_t)m * m);
+    std::vector<uint32_t> Mi((size_t)m * m);
+    for (int i = 0; i < m * m; ++i) {
+        M[i] = entry(lo, i);
+        if (integer) Mi[i] = (uint32_t)*reinterpret_cast<const int32_t *>(W + off[lo] + (size_t)i * es);
+    }
+    for (int k = lo + 1; k <= hi; ++k) {
+        const int c = radices[k], mc = m * c;
+        std::vector<std::complex<double>> N((size_t)mc * mc);
+        std::vector<uint32_t> Ni((size_t)mc * mc);
+        for (int i1 = 0; i1 < m; ++i1)
+            for (int j1 = 0; j1 < m; ++j1)
+                for (int i2 = 0; i2 < c; ++i2)
+                    for (int j2 = 0; j2 < c; ++j2) {
+                        const size_t o = (size_t)(i1 * c + i2) * mc + (j1 * c + j2);
+                        if (integer)
+                            Ni[o] = Mi[(size_t)i1 * m + j1] *
+                                    (uint32_t)*reinterpret_cast<const int32_t *>(W + off[k] + (size_t)(i2 * c + j2) * es);
+                        else
+                            N[o] = M[(size_t)i1 * m + j1] * entry(k, i2 * c + j2);
+                    }
+        M.swap(N);
+        Mi.swap(Ni);
+        m = mc;
+    }
+    std::vector<unsigned char> out((size_t)m * m * es);
+    for (int i = 0; i < m * m; ++i) {
+        unsigned char *p = out.data() + (size_t)i * es;
+        if (integer) {
+            const int32_t v = (int32_t)Mi[i];
+            memcpy(p, &v, 4);
+        } else if (dtype == GTT_F64) {
+            const double v = M[i].real();
+            memcpy(p, &v, 8);
+        } else if (dtype == GTT_F32) {
+            const float v = (float)M[i].real();
+            memcpy(p, &v, 4);
+        } else if (dtype == GTT_C64) {
+            const float v[2] = {(float)M[i].real(), (float)M[i].imag()};
+            memcpy(p, v, 8);
+        } else {
+            const double v[2] = {M[i].real(), M[i].imag()};
+            memcpy(p, v, 16);
+        }
+    }
+    return out;
+}
+
 // Copy W into the plan: one matrix, or for a mixed plan the factors
-// W_0, ..., W_{n-1} back to back (each pass gets its own W and W^H).
+// W_0, ..., W_{n-1} back to back (each pass gets its own W and W^H: a single
+// factor, or the Kronecker product of the adjacent factors it covers).
 static void set_w_bytes(gtt_plan_s *P, const void *W) {
     if (!P->mixed) {
         make_w_params((int)P->dtype, P->es, P->b, W, &P->Wf, &P->Wa);
@@ -255,8 +323,16 @@ static void set_w_bytes(gtt_plan_s *P, const void *W) {
     std::vector<size_t> off(n + 1, 0);  // byte offset of factor k
     for (int k = 0; k < n; ++k) off[k + 1] = off[k] + (size_t)P->radices[k] * P->radices[k] * P->es;
     for (PassPlan &pp : P->passes) {
-        const int k = pp.factor;
-        make_w_params((int)P->dtype, P->es, P->radices[k], (const unsigned char *)W + off[k], &pp.wf, &pp.wa);
+        const int hi = pp.factor, lo = pp.factor - pp.factors + 1;
+        if (pp.factors == 1) {
+            make_w_params((int)P->dtype, P->es, P->radices[hi], (const unsigned char *)W + off[hi], &pp.wf, &pp.wa);
+        } else {
+            const std::vector<unsigned char> K =
+                kron_factors((int)P->dtype, P->es, P->radices, off, (const unsigned char *)W, lo, hi);
+            int m = 1;
+            for (int k = lo; k <= hi; ++k) m *= P->radices[k];
+            make_w_params((int)P->dtype, P->es, m, K.data(), &pp.wf, &pp.wa);
+        }
     }
 }
 
@@ -404,30 +480,38 @@ extern "C" gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int 
         delete P;
         return cuda_error(e, "device query");
     }
-    // one pass per factor, the fastest index first: digit j of the natural
-    // index has radix b_{n-1-j} and stride L_j = prod_{i < j} b_{n-1-i}.  A tile
-    // is kblk consecutive blocks of b rows (a row every L elements) of a run of
-    // r contiguous elements: r the product of the lowest radices, kblk the
+    // passes over the digits, the fastest index first: digit j of the natural
+    // index has radix b_{n-1-j} and stride L_j = prod_{i < j} b_{n-1-i}.
+    // Adjacent digits whose radices multiply to at most 16 form one digit of
+    // that radix (d_j + b_j d_{j+1} + ...), transformed by the Kronecker
+    // product of their factors (the slower digit's factor on the left): one
+    // round trip instead of several, for more FMAs per element.  A tile is
+    // kblk consecutive blocks of B rows (a row every L elements) of a run of r
+    // contiguous elements: r the product of the lowest radices, kblk the
     // product of the next higher ones, as far as the default tile size allows
-    // (rows kblk * b at stride L address blocks hi .. hi + kblk - 1 in turn)
+    // (rows kblk * B at stride L address blocks hi .. hi + kblk - 1 in turn)
     const long long tmax = kDefaultTileBytes / P->es;
     auto rad = [&](int digit) { return (long long)radices[n - 1 - digit]; };
     long long L = 1;
-    for (int j = 0; j < n; ++j) {
-        const int k = n - 1 - j, bj = radices[k];
+    for (int j = 0; j < n;) {
+        int g = 1;
+        long long bj = rad(j);
+        while (j + g < n && bj * rad(j + g) <= 16) bj *= rad(j + g++);
         long long r = 1, kblk = 1;
         for (int i = 0; i < j && r * rad(i) * bj <= tmax; ++i) r *= rad(i);
-        for (int i = j + 1; i < n && kblk * rad(i) * bj * r <= tmax; ++i) kblk *= rad(i);
+        for (int i = j + g; i < n && kblk * rad(i) * bj * r <= tmax; ++i) kblk *= rad(i);
         PassPlan pp;
-        gtt_status_t st = build_pass_geom(P, bj, L, 1, kblk, r, 1, &pp);
+        gtt_status_t st = build_pass_geom(P, (int)bj, L, 1, kblk, r, 1, &pp);
         if (st != GTT_OK) {
             delete P;
             return st;
         }
         pp.m0 = j;
-        pp.factor = k;
+        pp.factor = n - 1 - j;
+        pp.factors = g;
         P->passes.push_back(pp);
         L *= bj;
+        j += g;
     }
     set_w_bytes(P, W);
     e = cudaMalloc(&P->dev_err, sizeof(int));

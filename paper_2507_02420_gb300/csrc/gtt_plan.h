@@ -51,8 +51,10 @@ struct PassPlan {
     std::string name;  // kernel name with its template arguments
     TmaPass tma;
     TcPass tc;
-    int factor = -1;                       // mixed plans: the factor W_k this pass applies
-    std::vector<unsigned char> wf, wa;     // mixed plans: that factor and its adjoint, parameter layout
+    int factor = -1;                       // mixed plans: the factor W_k of the pass's fastest digit
+    int factors = 1;                       // mixed plans: adjacent factors W_{factor-factors+1} .. W_factor,
+                                           // applied as their Kronecker product (one digit of their sizes' product)
+    std::vector<unsigned char> wf, wa;     // mixed plans: that matrix and its adjoint, parameter layout
 };
 
 // One pass of the backward schedule: the tile geometry (one stage per digit),

@@ -56,7 +56,16 @@ def test_mixed_forward_inverse_match_oracle(g, radices, dt, batch):
     ref = oracle.modes_mixed([up(W) for W in Ws], up(x))
     assert rel(y.cpu().numpy(), ref) <= TOL[dt]
     assert rel(xr.cpu().numpy(), up(x)) <= 2 * TOL[dt]   # unitary factors: the adjoint inverts
-    assert len(plan.describe()["passes"]) == len(radices)
+    # adjacent factors whose sizes multiply to at most 16 share a pass
+    want, j, digits = 0, 0, radices[::-1]
+    while j < len(digits):
+        m = digits[j]
+        j += 1
+        while j < len(digits) and m * digits[j] <= 16:
+            m *= digits[j]
+            j += 1
+        want += 1
+    assert len(plan.describe()["passes"]) == want
 
 
 def test_equal_factors_give_the_single_base_transform(g):
@@ -66,6 +75,22 @@ def test_equal_factors_give_the_single_base_transform(g):
     y_mixed = g.Plan.mixed([W] * 7, "c64", 2).forward(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = oracle.modes(up(W), up(x))
     assert rel(y_mixed, ref) <= 2e-6
+
+
+@pytest.mark.parametrize("radices,dt", [([2, 2, 2, 2], "c64"), ([3, 5, 2, 2, 3, 2], "f64"), ([2, 4, 2, 8], "c128"),
+                                         ([7, 2, 2, 3], "f32")])
+def test_merged_factors_match_oracle(g, radices, dt):
+    """Factors that share a pass (their Kronecker product as one factor) against
+    the oracle's factor-by-factor mode loop, forward and inverse."""
+    rng = np.random.default_rng(10050 + len(radices) + radices[0])
+    Ws, x = make(radices, 3, dt, rng)
+    plan = g.Plan.mixed(Ws, dt, 3)
+    assert len(plan.describe()["passes"]) < len(radices)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    ref = oracle.modes_mixed([up(W) for W in Ws], up(x))
+    assert rel(y.cpu().numpy(), ref) <= TOL[dt]
+    assert rel(plan.inverse(y).cpu().numpy(), up(x)) <= 2 * TOL[dt]
 
 
 def test_mixed_integer_arithmetic_is_exact(g):
