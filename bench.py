@@ -134,10 +134,11 @@ def gpu_smi_id(dev_index: int) -> str:
 
 
 # --------------------------------------------------------- oracle baseline
-def oracle_pairs_gelems(W, x, min_seconds: float, max_reps: int = 64):
-    """Time the FP64 oracle (forward + inverse pairs) on the host cores."""
+def oracle_pairs_gelems(W, x, min_seconds: float, max_reps: int = 64, threads: int | None = None):
+    """Time the FP64 oracle (forward + inverse pairs) on the host cores (all of
+    them unless `threads` is given)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     Wc = W.astype(np.complex128)
     xc = x.astype(np.complex128)
     reps, t0 = 0, time.perf_counter()
@@ -196,6 +197,53 @@ def run_reference(args, rank):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------- oracle leg (host cores)
+# Every use of the FP64 oracle in the GPU arm happens here, after all device
+# timing: the CPU baseline (all cores and one core), the naive O(N^2) oracle
+# of the b = 2, n = 12 workload, and the error of every timed result against
+# the oracle (GPU outputs are copied to host memory by the timed code and
+# checked here; large workloads on sampled vectors).
+ORACLE_CHECKS = []   # (where, key, fn) -> fn() returns the value stored at where[key]
+
+
+def oracle_check(where: dict, key: str, fn):
+    ORACLE_CHECKS.append((where, key, fn))
+
+
+def rel_l2(a, ref) -> float:
+    a = np.asarray(a)
+    ref = np.asarray(ref)
+    up = np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(ref) else np.float64
+    return float(np.linalg.norm(a.astype(up) - ref.astype(up)) / np.linalg.norm(ref.astype(up)))
+
+
+def oracle_modes(W, x, adjoint: bool = False):
+    import oracle
+    up = np.complex128 if np.iscomplexobj(W) or np.iscomplexobj(x) else np.float64
+    f = oracle.adjoint if adjoint else oracle.modes
+    return f(np.asarray(W).astype(up), np.asarray(x).astype(up))
+
+
+def run_oracle_leg(line: dict, W, x, args):
+    """cpu_baseline (oracle on all host cores, and on one core) and the errors
+    of the GPU results against the oracle."""
+    v, cores, reps, el = oracle_pairs_gelems(W, x, args.cpu_seconds)
+    v1, _, reps1, el1 = oracle_pairs_gelems(W, x, args.cpu_seconds_single, threads=1)
+    line["cpu_baseline"] = {
+        "value": v, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+        "sample": f"{reps} forward+inverse pair(s) of the full b=4, n=13 vector, complex128 mode loop, "
+                  f"{el:.1f} s",
+        "single_core": {"value": v1, "unit": "Gelem/s", "cores": 1,
+                        "sample": f"{reps1} forward+inverse pair(s) of the same vector on one thread, "
+                                  f"{el1:.1f} s"}}
+    for where, key, fn in ORACLE_CHECKS:
+        try:
+            where[key] = fn()
+        except Exception as e:  # a check that cannot run is reported, not fatal
+            where[key] = f"error: {e}"
+    ORACLE_CHECKS.clear()
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -411,7 +459,14 @@ def run_gpu(args, rank, world, local_rank):
 
     elapsed_s = elapsed_ms / 1e3
     value = whole_job_gelems(world, args.steps, 2 * BATCH * N, elapsed_s)
-    alg_bytes_step = 2 * len(passes) * bytes_per_launch  # fwd + inv
+    # algorithmic bytes: one read and one write of the data per transform
+    alg_bytes_step = 2 * bytes_per_launch  # fwd + inv
+    # the schedule's own HBM traffic: one round trip per pass
+    pass_bytes_step = 2 * len(passes) * bytes_per_launch
+    # the FP32 floor of the CUDA-core formulation: n modes x 4b real FMA per
+    # complex element, per transform
+    fma_s_step = 2 * BATCH * N * NDIG * 4 * B / (SMS * FP32_LANES * sm_mhz_max * 1e6)
+    hbm_s_step = alg_bytes_step / (hbm_peak * 1e9)
     line = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
@@ -426,19 +481,31 @@ def run_gpu(args, rank, world, local_rank):
                    "autotune cache" if cached else f"autotuned at plan time ({t_tune:.1f} s, untimed)"},
         "hbm_gbs_step": alg_bytes_step * args.steps / elapsed_s / 1e9,
         "hbm_frac_step": alg_bytes_step * args.steps / elapsed_s / 1e9 / hbm_peak,
+        "hbm_frac_step_basis": "one read + one write of the 512 MiB vector per transform, two transforms "
+                               "per step, against the measured copy bandwidth",
+        "traffic_frac_step": pass_bytes_step * args.steps / elapsed_s / 1e9 / hbm_peak,
+        "traffic_frac_step_basis": "one round trip per pass of the schedule",
+        "fp32_floor_frac_step": fma_s_step * args.steps / elapsed_s,
+        "fp32_floor_frac_step_basis": f"{NDIG} modes x {4 * B} real FMA per complex element per transform "
+                                      f"at the FP32 peak ({SMS} SMs x {FP32_LANES} lanes x {sm_mhz_max:.0f} MHz)",
+        "binding_floor_ms_per_step": max(fma_s_step, hbm_s_step) * 1e3,
         "inverse_roundtrip_rel_l2": err,
+        "tolerance": {"forward_rel_l2": 1e-5, "inverse_roundtrip_rel_l2": 2e-5},
         "clocks": clocks,
         "gpu_launches": launches_total,
         "roofline": roof,
         "e2e": e2e,
     }
+    if not args.no_cpu_baseline and world == 1:
+        y_host = yd.cpu().numpy()
+        oracle_check(line, "forward_rel_l2_vs_oracle",
+                     lambda: rel_l2(y_host, oracle_modes(W, x)))
+    del xd, yd, zd
+    torch.cuda.empty_cache()
     if not args.no_extras and world == 1:
         line["extras"] = run_extras(g, dev, peaks)
     if not args.no_cpu_baseline and world == 1:
-        v, cores, reps, el = oracle_pairs_gelems(W, x, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{reps} forward+inverse pair(s) of the full b=4, n=13 "
-                                          f"vector, complex128 mode loop, {el:.1f} s"}
+        run_oracle_leg(line, W, x, args)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -465,6 +532,8 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
     import torch
     W2, x2 = gi.workload_inputs("b16_n6_batch64_f32", batch=batch)
     x2d = torch.from_numpy(x2).to(dev)
+    items = sorted({0, batch // 3, (2 * batch) // 3, batch - 1})
+    x_items = x2[items].copy()
     del x2
     n2 = x2d.numel()
     res = {}
@@ -488,8 +557,13 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
     p64 = g.Plan(W2.astype(np.float64), 6, "f64", batch)
     y64 = p64.forward(x2d.double())
     for name, y in outs.items():
-        res[name]["rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(y.double() - y64) /
-                                            torch.linalg.vector_norm(y64))
+        res[name]["rel_l2_vs_fp64_gpu"] = float(torch.linalg.vector_norm(y.double() - y64) /
+                                                torch.linalg.vector_norm(y64))
+        y_items = y[items].cpu().numpy()
+        oracle_check(res[name], "rel_l2_vs_oracle",
+                     lambda yi=y_items: rel_l2(yi, oracle_modes(W2, x_items)))
+        res[name]["oracle_items"] = items
+        res[name]["tolerance"] = 1e-6
     best = lambda k: min(v["ms"] for kk, v in res.items() if kk.startswith(k))  # noqa: E731
     res["bf16x3_speedup_over_fp32"] = best("fp32_cuda_core") / best("bf16x3_tcgen05")
     del x2d, outs, y64, p64
@@ -515,8 +589,11 @@ def extra_train(g, dev, hbm, reps=10):
 
     def train_step():
         p3.forward(x3d, out=y3d)
-        p3.backward(x3d, dy3)
+        return p3.backward(x3d, dy3)
     t = _time_device(train_step, reps=reps)
+    dx3, dW3 = train_step()
+    y_h, dx_h, dW_h = y3d.cpu().numpy(), dx3.cpu().numpy(), dW3.cpu().numpy()
+    dy_h = dy3.cpu().numpy()
     p3.set_chunking(-1)
     tc = _time_device(lambda: p3.forward(x3d, out=y3d), reps=reps)
     p3.set_chunking(0)
@@ -532,8 +609,17 @@ def extra_train(g, dev, hbm, reps=10):
            "roofline": {"floor_ms": floor * 1e3, "frac": floor / t, "bound": "alu" if t_fma > t_mem else "hbm",
                         "basis": "max(5 x 4 B per element of HBM traffic, 4*n*b FMAs per element at the FP32 peak)"},
            "includes": "gtt_forward + gtt_backward (dx and dW)", "schedule": "autotuned at plan time (untimed)",
-           "forward_ms": tf * 1e3, "forward_l2chunked_ms": tc * 1e3}
-    del x3d, y3d, dy3, p3
+           "forward_ms": tf * 1e3, "forward_l2chunked_ms": tc * 1e3,
+           "tolerance": {"forward": 1e-5, "dx": 1e-5, "dW": 1e-4}}
+
+    def grad_errors():
+        import oracle
+        W64 = W3.astype(np.float64)
+        rdx, rdW = oracle.grad(W64, x3.astype(np.float64), dy_h.astype(np.float64))
+        return {"forward": rel_l2(y_h, oracle_modes(W3, x3)), "dx": rel_l2(dx_h, rdx), "dW": rel_l2(dW_h, rdW),
+                "basis": "whole batch (32 vectors), oracle gradient in FP64"}
+    oracle_check(res, "rel_l2_vs_oracle", grad_errors)
+    del x3d, y3d, dy3, p3, dx3, dW3
     torch.cuda.empty_cache()
     return res
 
@@ -559,11 +645,22 @@ def extra_grouped(g, dev, hbm, reps=10, count=1000):
     t = _time_device(grp.execute, reps=reps)
     grp.check()
     d = grp.describe()
-    return {"ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
+    sample = list(range(0, len(reqs), max(1, len(reqs) // 25)))
+    got = [(reqs[i]["W"], reqs[i]["x"].cpu().numpy(), reqs[i]["y"].cpu().numpy(), reqs[i]["dtype"]) for i in sample]
+
+    def grouped_errors():
+        errs = {"f32": [], "c64": []}
+        for Wr, xr, yr, dt in got:
+            errs[dt].append(rel_l2(yr, oracle_modes(Wr, xr)))
+        return {dt: max(v) for dt, v in errs.items() if v} | {"requests_checked": len(got), "statistic": "max over requests"}
+    out = {"ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
             "kernel_launches_per_execute": 1, "work_items": d["work_items"],
             "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9,
             "roofline": {"floor_ms": floor * 1e3, "frac": floor / t,
-                         "basis": "sum over requests of max(one HBM round trip, n*N*b FMAs (x4 complex) at the FP32 peak)"}}
+                         "basis": "sum over requests of max(one HBM round trip, n*N*b FMAs (x4 complex) at the FP32 peak)"},
+           "tolerance": {"f32": 2e-6, "c64": 2e-6}}
+    oracle_check(out, "rel_l2_vs_oracle", grouped_errors)
+    return out
 
 
 def extra_filter(g, dev, hbm, reps=10):
@@ -579,8 +676,16 @@ def extra_filter(g, dev, hbm, reps=10):
     tf = _time_device(lambda: plan.filter(xd, N // 2, True, out=yd), reps=reps)
     tp = _time_device(lambda: (plan.forward(xd, out=yd), plan.inverse(yd, out=yd)), reps=reps)
     plan.check()
+    plan.filter(xd, N // 2, True, out=yd)
+    y_h = yd.cpu().numpy()
     res = {"ms": tf * 1e3, "gelem_s": BATCH * N / tf / 1e9, "cut": N // 2,
-           "forward_plus_inverse_ms": tp * 1e3, "overhead_vs_forward_plus_inverse": tf / tp - 1}
+           "forward_plus_inverse_ms": tp * 1e3, "overhead_vs_forward_plus_inverse": tf / tp - 1,
+           "tolerance": 2e-5}
+
+    def filter_error():
+        import oracle
+        return rel_l2(y_h, oracle.filter(W.astype(np.complex128), x.astype(np.complex128), N // 2, True))
+    oracle_check(res, "rel_l2_vs_oracle", filter_error)
     del xd, yd, plan
     torch.cuda.empty_cache()
     return res
@@ -603,8 +708,19 @@ def extra_codec(g, dev, hbm, reps=10, k=1024):
     td = _time_device(lambda: plan.decompress(idx, val, out=yd), reps=reps)
     plan.check()
     F = float((val.abs() ** 2).sum() / (xd.abs() ** 2).sum())
+    idx_h, val_h, rec_h = idx.cpu().numpy(), val.cpu().numpy(), yd.cpu().numpy()
     res = {"k": k, "compress_ms": tc * 1e3, "decompress_ms": td * 1e3,
-           "compress_gelem_s": BATCH * N / tc / 1e9, "kept_energy_fraction": F}
+           "compress_gelem_s": BATCH * N / tc / 1e9, "kept_energy_fraction": F, "tolerance": 1e-5}
+
+    def codec_errors():
+        import oracle
+        spec = oracle_modes(W, x)
+        ref_val = np.take_along_axis(spec, idx_h, axis=1)
+        ref_rec = oracle.reconstruct(W.astype(np.complex128), idx_h, ref_val, N)
+        # the kept set itself is checked bit-exactly in the GPU tests (ties are
+        # decided in the plan's precision); here: values and reconstruction
+        return {"kept_values": rel_l2(val_h, ref_val), "reconstruction": rel_l2(rec_h, ref_rec)}
+    oracle_check(res, "rel_l2_vs_oracle", codec_errors)
     del xd, spec, yd, plan
     torch.cuda.empty_cache()
     return res
@@ -625,14 +741,67 @@ def extra_mixed(g, dev, hbm, reps=10, batch=16):
     t = _time_device(lambda: plan.forward(xd, out=yd), reps=reps)
     plan.check()
     passes = len(plan.describe()["passes"])
+    y0 = yd[0].cpu().numpy()
     res = {"radices": radices, "batch": batch, "ms": t * 1e3, "gelem_s": batch * Nm / t / 1e9,
-           "passes": passes, "hbm_frac_if_passes_from_hbm": passes * 2 * batch * Nm * 8 / t / 1e9 / hbm}
+           "passes": passes, "hbm_frac_if_passes_from_hbm": passes * 2 * batch * Nm * 8 / t / 1e9 / hbm,
+           "tolerance": 2e-6}
+
+    def mixed_error():
+        import oracle
+        return rel_l2(y0, oracle.modes_mixed([Wk.astype(np.complex128) for Wk in Ws], x[:1].astype(np.complex128))[0])
+    oracle_check(res, "rel_l2_vs_oracle_vector_0", mixed_error)
     del xd, yd, plan
     torch.cuda.empty_cache()
     return res
 
 
-EXTRAS = {"b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_train_step", extra_train),
+def extra_b2_f64(g, dev, hbm, reps=20):
+    """b = 2, n = 12 (N = 4096), batch 1, FP64, W = H / sqrt(2): a latency-bound
+    single-vector transform (no roofline fraction).  GPU forward + inverse time
+    (median of `reps` single calls after 5 warm-ups, CUDA events), and in the
+    oracle leg the naive O(N^2) dense oracle and the mode-loop oracle, each
+    timed, with the GPU result's error against the dense oracle."""
+    import torch
+    W0, x0 = gi.workload_inputs("b2_n12_f64")
+    plan = g.Plan(W0, 12, "f64", 1)
+    xd = torch.from_numpy(x0).to(dev)
+    yd, zd = torch.empty_like(xd), torch.empty_like(xd)
+    times = {"forward": [], "forward_plus_inverse": []}
+    for k in range(5 + reps):
+        s, m, e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s.record()
+        plan.forward(xd, out=yd)
+        m.record()
+        plan.inverse(yd, out=zd)
+        e.record()
+        torch.cuda.synchronize()
+        if k >= 5:
+            times["forward"].append(s.elapsed_time(m) * 1e3)
+            times["forward_plus_inverse"].append(s.elapsed_time(e) * 1e3)
+    plan.check()
+    y_h, z_h = yd.cpu().numpy(), zd.cpu().numpy()
+    res = {"gpu_forward_us": statistics.median(times["forward"]),
+           "gpu_forward_plus_inverse_us": statistics.median(times["forward_plus_inverse"]),
+           "statistic": f"median of {reps} calls after 5 warm-ups", "passes": len(plan.describe()["passes"]),
+           "tolerance": 1e-13}
+
+    def dense_leg():
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.dense(W0.astype(np.complex128), x0[0].astype(np.complex128))
+        t_dense = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(20):
+            oracle.modes(W0, x0, threads=1)
+        t_modes = (time.perf_counter() - t0) / 20
+        return {"forward_rel_l2_vs_dense": rel_l2(y_h[0], ref.real),
+                "roundtrip_rel_l2": rel_l2(z_h, x0),
+                "dense_oracle_forward_s": t_dense, "mode_loop_oracle_forward_us_1_core": t_modes * 1e6}
+    oracle_check(res, "oracle", dense_leg)
+    return res
+
+
+EXTRAS = {"b2": ("b2_n12_f64", extra_b2_f64), "b16": ("b16_n6_batch64_f32", extra_b16), "train": ("b8_n7_batch32_train_step", extra_train),
           "grouped": ("grouped_1000_uneven", extra_grouped), "filter": ("b4_n13_c64_lowpass_filter", extra_filter),
           "codec": ("b4_n13_c64_topk_codec", extra_codec), "mixed": ("mixed_radix_9_factors_c64", extra_mixed)}
 
@@ -647,6 +816,8 @@ def run_extras(g, dev, peaks, only=None, reps=10, b16_batch=64, grouped_requests
         if only is None or key == only:
             if key == "b16":
                 out[name] = fn(g, dev, hbm, reps, b16_batch)
+            elif key == "b2":
+                out[name] = fn(g, dev, hbm, max(reps, 20))
             elif key == "grouped":
                 out[name if grouped_requests == 1000 else f"grouped_{grouped_requests}_uneven"] = \
                     fn(g, dev, hbm, reps, grouped_requests)
@@ -678,6 +849,8 @@ def main():
     ap.add_argument("--tune-cache", default=None,
                     help="autotune cache file: reused if it exists, else written after tuning")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-seconds-single", type=float, default=5.0,
+                    help="minimum seconds of the one-core oracle timing (at least one pair)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -231,7 +231,9 @@ gtt_status_t gtt_inverse(gtt_plan_t plan, const void *y, void *x, gtt_stream_t s
  *   dW       device, b*b elements of the element type, row-major, or NULL;
  *            overwritten with the sum over the whole batch.  The sum is taken
  *            in a fixed order, so repeated calls give identical bits.
- * dx may alias dy.  Floating-point dtypes only (GTT_ERR_UNSUPPORTED for I32).
+ * dx may alias dy but not x_saved (GTT_ERR_INVALID_ARG: a checkpoint may be
+ * written to dx before x_saved is read for the last time).  Floating-point
+ * dtypes only (GTT_ERR_UNSUPPORTED for I32).
  */
 gtt_status_t gtt_backward(gtt_plan_t plan, const void *x_saved, const void *dy, void *dx, void *dW,
                           gtt_stream_t stream);
@@ -244,18 +246,20 @@ gtt_status_t gtt_backward(gtt_plan_t plan, const void *x_saved, const void *dy, 
  * reserved the device's memory (where a stray cudaMalloc can fail or fragment
  * the pool), or latency-critical loops where cudaMalloc/cudaFree would
  * synchronize the device.
- *   x, dy, dW as in gtt_backward.  dx is required (non-NULL) and must not
- *   alias dy: it also holds the checkpoint between the two backward passes.
- * Scratch: the dW partials live in a fixed 2 MiB array in the library's
- * device globals (held by every GPU that loads the library until exit).  The
- * first call on a device looks up that array's device address (with the
- * plan's device current) and builds the plan's backward schedule on the host;
- * make that first call before any stream capture.  All calls share the
- * array and each overwrites what it reads; calls whose kernels overlap on the
- * GPU (other streams, other plans) race on it and must be serialised.
- * Errors: GTT_ERR_INVALID_ARG when dx is NULL or aliases dy, when the
+ *   x, dy, dW as in gtt_backward.  dx is required (non-NULL) and must alias
+ *   neither dy nor x: it also holds the checkpoint between the two backward
+ *   passes.  The kernels and their order are those of gtt_backward with the
+ *   same dx, so dx and dW are bitwise equal to gtt_backward's.
+ * Scratch: the dW partials live in a fixed 1 MiB array in the library's
+ * device globals (held by every GPU that loads the library until exit).
+ * Every call looks up that array's device address with the plan's device
+ * current; the first call also builds the plan's backward schedule on the
+ * host, so make that first call before any stream capture.  All calls share
+ * the array and each overwrites what it reads; calls whose kernels overlap on
+ * the GPU (other streams, other plans) race on it and must be serialised.
+ * Errors: GTT_ERR_INVALID_ARG when dx is NULL or aliases dy or x, when the
  * transform needs more than two backward passes (a data-sized checkpoint),
- * or when its dW partials exceed the 2 MiB array; otherwise as gtt_backward.
+ * or when its dW partials exceed the 1 MiB array; otherwise as gtt_backward.
  */
 gtt_status_t gtt_backward_noalloc(gtt_plan_t plan, const void *x_saved, const void *dy, void *dx,
                                   void *dW, gtt_stream_t stream);

@@ -26,6 +26,7 @@ Routes (each cites the passage it follows; the C source has the details):
 * ``modes_mixed(Ws, x)``    -- the same transform one factor at a time: W_k
                                applied along axis k of x viewed as
                                [b_0, ..., b_{n-1}] (axis 0 most significant)
+* ``modes_mixed_u32(Ws, x)``-- that loop on int32 data, arithmetic mod 2^32
 * ``filter(W, x, cut, low)`` -- natural-order filtering (Sec. 4.3.2): the
                                spectrum G_N x, coefficients with index >= cut
                                (low-pass) or < cut (high-pass) set to zero,
@@ -250,6 +251,30 @@ def modes_mixed(Ws, x) -> np.ndarray:
     for k, W in enumerate(Ws):
         t = np.moveaxis(np.tensordot(W, t, axes=([1], [k + 1])), 0, k + 1)
     return t.reshape(x.shape)
+
+
+def modes_mixed_u32(Ws, x) -> np.ndarray:
+    """The heterogeneous transform on int32 data with arithmetic modulo 2^32
+    (the integer reading of the remark after Def. 2.3): the same factor-by-
+    factor loop as ``modes_mixed``, on unsigned 64-bit integers reduced mod
+    2^32 after every factor.  Every product of two values below 2^32 fits
+    64 bits and 2^32 divides 2^64, so a wrapped 64-bit sum is still exact
+    modulo 2^32.  Returns uint32 (the bit patterns of the int32 result)."""
+    mask = np.uint64(0xFFFFFFFF)
+    Ws = [np.asarray(np.asarray(W).astype(np.int64) & 0xFFFFFFFF, dtype=np.uint64) for W in Ws]
+    x = np.atleast_2d(np.asarray(np.asarray(x).astype(np.int64) & 0xFFFFFFFF, dtype=np.uint64))
+    dims = [W.shape[0] for W in Ws]
+    t = x.reshape([x.shape[0]] + dims)
+    for k, W in enumerate(Ws):
+        t = np.moveaxis(t, k + 1, -1)          # axis k last: [..., b_k]
+        acc = np.zeros(t.shape, dtype=np.uint64)
+        for i in range(W.shape[0]):
+            s = np.zeros(t.shape[:-1], dtype=np.uint64)
+            for j in range(W.shape[1]):
+                s = (s + W[i, j] * t[..., j]) & mask
+            acc[..., i] = s
+        t = np.moveaxis(acc, -1, k + 1)
+    return np.ascontiguousarray(t.reshape(x.shape).astype(np.uint32))
 
 
 def filter(W, x, cut: int, keep_low: bool = True, threads: int | None = None) -> np.ndarray:

@@ -4,8 +4,16 @@ GTTFunction.apply(x, W, n) takes x of shape [batch, N] on a CUDA device and a
 b x b W (trainable).  The forward calls gtt_forward; the backward calls
 gtt_backward, which returns dL/dx = (W^H)^{(x)n} dL/dy and dL/dW as a per-mode
 reduction of fibre outer products (PyTorch's conjugate convention for complex
-types).  W's values are copied to the host on every forward (the kernels read
-W from their constant bank).
+types).  The kernels read W from their constant bank, so its values have to
+be on the host when a kernel is launched: the wrapper copies W to the host only
+when it may differ from the last copy the plan took.  The plan's cache keeps a
+detached alias of the W it copied (so that storage cannot be freed and reused
+by another tensor) and the version counter it had; W is copied again when it
+lives in another storage or when an in-place update has bumped the counter (an
+optimizer step does).  A forward or backward with an unchanged W therefore
+neither copies W nor waits for the device.  Changes that bypass the version
+counter (writes through ``W.data``) are not seen: pass a fresh tensor instead
+(``W.clone()``), as a finite-difference gradient check must.
 """
 from __future__ import annotations
 
@@ -22,12 +30,15 @@ _lock = threading.Lock()
 def _plan_for(W: torch.Tensor, n: int, x: torch.Tensor) -> Plan:
     key = (int(W.shape[0]), int(n), x.dtype, int(x.shape[0]), x.device.index)
     with _lock:
-        plan = _cache.get(key)
-        if plan is None:
+        entry = _cache.get(key)
+        if entry is None:
             plan = Plan(W.detach().cpu(), n, dtype_code(x.dtype), int(x.shape[0]))
-            _cache[key] = plan
-        else:
+            _cache[key] = [plan, W.detach(), W._version]
+            return plan
+        plan, held, version = entry
+        if W.data_ptr() != held.data_ptr() or W.dtype != held.dtype or W._version != version:
             plan.set_w(W.detach().cpu())
+            entry[1], entry[2] = W.detach(), W._version
     return plan
 
 

@@ -119,6 +119,7 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
     if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "not available for mixed-radix plans");
     if (P->dtype == GTT_I32) return set_error(GTT_ERR_UNSUPPORTED, "backward needs a floating-point dtype");
     if (!x || !dy) return set_error(GTT_ERR_INVALID_ARG, "NULL x or dy");
+    if (dx && dx == x) return set_error(GTT_ERR_INVALID_ARG, "dx must not alias x_saved");
     auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
     if (!al(x) || !al(dy) || (dx && !al(dx)) || (dW && !al(dW)))
         return set_error(GTT_ERR_INVALID_ARG, "pointers must be 16-byte aligned");

@@ -781,7 +781,20 @@ extern "C" gtt_status_t gtt_plan_timing(gtt_plan_t P, char *buf, size_t len) {
                  k ? ", " : "", names[k].c_str(), counts[k], total[k]);
         s += tmp;
     }
-    s += "]}";
+    s += "]";
+    if (P->bwd_ready) {  // the backward schedule, once a backward call has built it
+        s += ", \"backward\": [";
+        for (size_t i = 0; i < P->bwd.size(); ++i) {
+            const BwdPass &bp = P->bwd[i];
+            char tmp[384];
+            snprintf(tmp, sizeof tmp,
+                     "%s{\"kernel\": \"%s\", \"m0\": %d, \"g\": %d, \"r\": %lld, \"grid\": %d, \"smem\": %zu}",
+                     i ? ", " : "", bp.name.c_str(), bp.geo.m0, bp.g, bp.geo.r, bp.grid, bp.smem);
+            s += tmp;
+        }
+        s += "]";
+    }
+    s += "}";
     snprintf(buf, len, "%s", s.c_str());
     return st;
 }
@@ -862,7 +875,20 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                  t ? "true" : "false", t ? pp.tma.params.nbuf : 0);
         s += tmp;
     }
-    s += "]}";
+    s += "]";
+    if (P->bwd_ready) {  // the backward schedule, once a backward call has built it
+        s += ", \"backward\": [";
+        for (size_t i = 0; i < P->bwd.size(); ++i) {
+            const BwdPass &bp = P->bwd[i];
+            char tmp[384];
+            snprintf(tmp, sizeof tmp,
+                     "%s{\"kernel\": \"%s\", \"m0\": %d, \"g\": %d, \"r\": %lld, \"grid\": %d, \"smem\": %zu}",
+                     i ? ", " : "", bp.name.c_str(), bp.geo.m0, bp.g, bp.geo.r, bp.grid, bp.smem);
+            s += tmp;
+        }
+        s += "]";
+    }
+    s += "}";
     snprintf(buf, len, "%s", s.c_str());
     return GTT_OK;
 }

@@ -7,19 +7,21 @@
 // would synchronize the device.  gtt_backward allocates its dW-partial
 // scratch (and, in some cases, data-sized work buffers) on first use; this
 // variant takes the dW-partial scratch from a fixed array in the library's
-// own device globals and needs no data-sized buffer.
+// own device globals and needs no data-sized buffer.  It launches the same
+// kernels in the same order as gtt_backward with a caller-provided dx (the
+// checkpoint pass on the TMA kernel where the geometry allows it), so its
+// results are bitwise equal to gtt_backward's.
 //
 // The scratch is a file-scope `static __device__` array of
 // kNoAllocScratchBytes; every GPU that loads the library keeps it until the
 // process exits.  In host code the array's name is only a host-side stand-in,
-// so its device address is obtained once per device with
-// cudaGetSymbolAddress (on the first call on that device, with the device
-// current) and passed to the kernels.  All calls share the one array:
-// calls whose kernels overlap on the GPU (different streams, or different
-// plans on the same device at the same time) race on it.  Every call
-// overwrites the partials it reads, so nothing has to start at zero.
+// so every call looks up its device address with cudaGetSymbolAddress (with
+// the plan's device current; no address is cached, so a reset context cannot
+// leave a stale one) and passes it to the kernels.  All calls share the one
+// array: calls whose kernels overlap on the GPU (different streams, or
+// different plans on the same device at the same time) race on it.  Every
+// call overwrites the partials it reads, so nothing has to start at zero.
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "gtt_bwd.cuh"
@@ -29,23 +31,15 @@ using namespace gtt;
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 2u << 20;  // 2 MiB of dW partials
+constexpr size_t kNoAllocScratchBytes = 1u << 20;  // 1 MiB of dW partials
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
-
-gtt_status_t scratch_address(int dev, void **out) {
-    if (dev < 0 || dev >= kMaxDevices) return set_error(GTT_ERR_UNSUPPORTED, "device index above 63");
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the static scratch");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+// Device address of g_noalloc_scratch on the current device.
+gtt_status_t scratch_address(void **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the static scratch");
+    *out = p;
     return GTT_OK;
 }
 
@@ -59,6 +53,7 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
     if (!x || !dy || !dx)
         return set_error(GTT_ERR_INVALID_ARG, "gtt_backward_noalloc needs x, dy and dx (dx holds its checkpoint)");
     if (dx == dy) return set_error(GTT_ERR_INVALID_ARG, "gtt_backward_noalloc needs dx distinct from dy");
+    if (dx == x) return set_error(GTT_ERR_INVALID_ARG, "gtt_backward_noalloc needs dx distinct from x");
     auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
     if (!al(x) || !al(dy) || !al(dx) || (dW && !al(dW)))
         return set_error(GTT_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
@@ -68,7 +63,7 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
     if (dev != P->device) return set_error(GTT_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");
     gtt_status_t st;
     void *scratch = nullptr;
-    st = scratch_address(dev, &scratch);
+    st = scratch_address(&scratch);
     if (st != GTT_OK) return st;
     if (!P->bwd_ready) {
         st = make_bwd_schedule(P, kBwdSmemBudget);  // host-side set-up, no allocation on the device
@@ -93,13 +88,17 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
     for (int j = m - 1; j >= 0; --j) {
         const BwdPass &bp = P->bwd[j];
         const void *A = x;
-        if (j == 1) {
-            const PassPlan &fp = P->bwd[0].fwd;
+        if (j == 1) {  // a^(1) = forward pass 0 of the backward schedule, into dx
+            PassPlan &fp = P->bwd[0].fwd;
             const void *in = x;
             void *outp = CK;
-            void *args[4] = {(void *)&in, (void *)&outp, (void *)&fp.params, (void *)Wf.data()};
-            e = cudaLaunchKernel(fp.kern, dim3(fp.grid), dim3(fp.block), args, fp.smem, s);
-            if (e != cudaSuccess) return cuda_error(e, "checkpoint pass launch");
+            if (fp.tma.on) {
+                st = tma_run(P, fp, Wf, in, outp, s, 0, fp.params.tiles);
+            } else {
+                void *args[4] = {(void *)&in, (void *)&outp, (void *)&fp.params, (void *)Wf.data()};
+                st = launch_timed(P, fp.kern, dim3(fp.grid), dim3(fp.block), args, fp.smem, s, fp.name);
+            }
+            if (st != GTT_OK) return st;
             A = CK;
         }
         const void *Gin = (j == m - 1) ? dy : (const void *)dx;
@@ -108,8 +107,8 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
         int g = bp.g;
         void *args[8] = {(void *)&A, (void *)&Gin, (void *)&Gout, (void *)&dwp,
                          (void *)&bp.geo.params, (void *)&g, (void *)Wf.data(), (void *)Wa.data()};
-        e = cudaLaunchKernel(bp.kern, dim3(bp.grid), dim3(kBwdThreads), args, bp.smem, s);
-        if (e != cudaSuccess) return cuda_error(e, "backward pass launch");
+        st = launch_timed(P, bp.kern, dim3(bp.grid), dim3(kBwdThreads), args, bp.smem, s, bp.name);
+        if (st != GTT_OK) return st;
         part_off += bp.grid;
     }
     if (dW) {
@@ -117,8 +116,9 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
         const void *parts = scratch;
         int bb = P->b * P->b;
         void *args[4] = {(void *)&parts, (void *)&nparts, (void *)&bb, (void *)&dW};
-        e = cudaLaunchKernel(rk, dim3((bb + kDwEntriesPerBlock - 1) / kDwEntriesPerBlock), dim3(32 * kDwEntriesPerBlock), args, 0, s);
-        if (e != cudaSuccess) return cuda_error(e, "dW reduction launch");
+        st = launch_timed(P, rk, dim3((bb + kDwEntriesPerBlock - 1) / kDwEntriesPerBlock), dim3(32 * kDwEntriesPerBlock),
+                          args, 0, s, "gtt_dw_reduce_kernel");
+        if (st != GTT_OK) return st;
     }
     return GTT_OK;
 }

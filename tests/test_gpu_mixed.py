@@ -105,6 +105,25 @@ def test_mixed_integer_arithmetic_is_exact(g):
     np.testing.assert_array_equal(y.astype(np.int64), np.rint(ref).astype(np.int64))
 
 
+@pytest.mark.parametrize("radices", [[3, 2, 5, 4], [2, 2, 2, 2, 3], [16, 7, 2, 8], [4, 4, 3]])
+def test_mixed_integer_wraps_modulo_2_32(g, radices):
+    """int32 factors and data over the whole 32-bit range, so products and sums
+    overflow: bit-exact against the oracle's mod-2^32 heterogeneous loop,
+    including passes that apply several adjacent factors as their Kronecker
+    product (formed modulo 2^32 on the host)."""
+    rng = np.random.default_rng(10250 + sum(radices))
+    Ws = [rng.integers(-2 ** 31, 2 ** 31, size=(b, b)).astype(np.int32) for b in radices]
+    N = int(np.prod(radices))
+    x = rng.integers(-2 ** 31, 2 ** 31, size=(3, N)).astype(np.int32)
+    plan = g.Plan.mixed(Ws, "i32", 3)
+    y = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.modes_mixed_u32(Ws, x)
+    np.testing.assert_array_equal(y.view(np.uint32), ref)
+    # the adjoint of an integer factor is its transpose
+    yi = plan.inverse(torch.from_numpy(x).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(yi.view(np.uint32), oracle.modes_mixed_u32([W.T for W in Ws], x))
+
+
 def test_mixed_set_w_filter_and_codec(g):
     rng = np.random.default_rng(10300)
     radices = [5, 4, 3, 8]

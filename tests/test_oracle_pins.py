@@ -73,6 +73,35 @@ def test_alg1_and_mode_loop_equal_definition(b):
                                rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("b", (2, 3, 4))
+def test_single_mode_pass_is_one_kronecker_factor(b):
+    """O4's building block: one mode-k pass applies W to digit k only, i.e. it is
+    the matrix I_{b^(n-1-k)} (x) W (x) I_{b^k} (Def. 2.3 with every other
+    factor the identity; digit k has stride b^k).  Composing the passes for
+    k = 0..n-1 gives W^{(x)n}.  A swapped digit (k <-> n-1-k), an off-by-one k,
+    or a transposed W fails."""
+    rng = np.random.default_rng(40 + b)
+    n = 4
+    N = b ** n
+    W = rand_c(rng, (b, b))          # general, non-unitary, non-symmetric
+    x = rand_c(rng, N)
+    cur = x
+    for k in range(n):
+        F = np.kron(np.kron(np.eye(b ** (n - 1 - k)), W), np.eye(b ** k))
+        y = oracle.mode_pass(W, x, k, threads=2)
+        np.testing.assert_allclose(y, F @ x, rtol=1e-12, atol=1e-12)
+        # the wrong digits give something else
+        for kk in {n - 1 - k, (k + 1) % n} - {k}:
+            Fk = np.kron(np.kron(np.eye(b ** (n - 1 - kk)), W), np.eye(b ** kk))
+            assert not np.allclose(y, Fk @ x, atol=1e-6)
+        Ft = np.kron(np.kron(np.eye(b ** (n - 1 - k)), W.T), np.eye(b ** k))
+        assert not np.allclose(y, Ft @ x, atol=1e-6)
+        cur = oracle.mode_pass(W, cur, k, threads=1)
+    np.testing.assert_allclose(cur, kron_power(W, n) @ x, rtol=1e-12, atol=1e-12)
+    with pytest.raises(RuntimeError):
+        oracle.mode_pass(W, x, n)
+
+
 def test_hadamard_closed_form():
     """Sec. 2.6: for W = H/sqrt(2), G_N(p,q) = (-1)^{p.q} / sqrt(N)."""
     n = 10
@@ -410,3 +439,28 @@ def test_mixed_mode_loop_is_the_kronecker_product():
     W = gi.haar_unitary(3, rng)
     x = gi.complex_normal_x((2, 3 ** 5), rng, np.complex128)
     np.testing.assert_allclose(oracle.modes_mixed([W] * 5, x), oracle.modes(W, x), atol=1e-12)
+
+
+def test_mixed_integer_route_wraps_like_python_ints():
+    """The uint32 heterogeneous loop equals exact big-integer arithmetic with
+    the Kronecker definition (remark after Def. 2.3), reduced mod 2^32, for
+    values whose partial sums overflow 32 bits.  A reversed factor order and a
+    transposed factor fail."""
+    rng = np.random.default_rng(72)
+    for radices in ([3, 2, 5, 4], [2, 2, 2, 2, 3], [7, 3]):
+        Ws = [rng.integers(-2 ** 31, 2 ** 31, size=(b, b)) for b in radices]
+        N = int(np.prod(radices))
+        x = rng.integers(-2 ** 31, 2 ** 31, size=(2, N))
+        G = np.array([[1]], dtype=object)
+        for W in Ws:
+            G = np.kron(G, W.astype(object))
+        ref = np.array([[int(v) % (1 << 32) for v in G.dot(xv.astype(object))] for xv in x],
+                       dtype=np.uint32)
+        got = oracle.modes_mixed_u32(Ws, x)
+        np.testing.assert_array_equal(got, ref)
+        assert not np.array_equal(oracle.modes_mixed_u32(Ws[::-1], x), ref)
+        assert not np.array_equal(oracle.modes_mixed_u32([Ws[0].T] + Ws[1:], x), ref)
+    # equal factors reduce to the single-base integer loop
+    W = rng.integers(-9, 10, size=(3, 3))
+    x = rng.integers(-2 ** 31, 2 ** 31, size=3 ** 5)
+    np.testing.assert_array_equal(oracle.modes_mixed_u32([W] * 5, x)[0], oracle.modes_u32(W, x))
