@@ -64,12 +64,17 @@ typedef enum {
     GTT_ERR_INTERNAL = 6
 } gtt_status_t;
 
-/* Arithmetic used for the b >= 16 contractions (gtt_plan_set_precision). */
+/* Arithmetic of the mode contractions (gtt_plan_set_precision). */
 typedef enum {
     GTT_PREC_AUTO = 0,   /* library choice, the default: BF16X3 for b = 16 FP32 with
                             n >= 3 (faster, and at least as accurate), else FP32      */
     GTT_PREC_FP32 = 1,   /* FP32 FMA on CUDA cores                                  */
-    GTT_PREC_BF16X3 = 2  /* tcgen05 BF16 products of 3-piece splits, FP32 accumulate */
+    GTT_PREC_BF16X3 = 2, /* tcgen05 BF16 products of 3-piece splits, FP32 accumulate */
+    GTT_PREC_TF32X3 = 3  /* complex64, b = 4, opt-in: pairs of digits as one base-16
+                            digit with W (x) W, tcgen05 TF32 products of 2-piece
+                            splits (three products), FP32 accumulate; the digits
+                            left over in each pass on CUDA cores in FP32; two HBM
+                            round trips for n = 13 (slower than FP32 on GB300)      */
 } gtt_precision_t;
 
 /*
@@ -120,13 +125,16 @@ gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int *radices, c
  * Calls already queued on a stream keep the W they were launched with. */
 gtt_status_t gtt_plan_set_w(gtt_plan_t plan, const void *W);
 
-/* Select the arithmetic of the b = 16 contraction (gtt_precision_t).  Other b
- * accept GTT_PREC_AUTO and GTT_PREC_FP32 only.  GTT_PREC_BF16X3 requires b = 16,
- * dtype F32 and n >= 3; otherwise GTT_ERR_UNSUPPORTED.  The tensor-core path has
- * one fixed schedule: gtt_plan_set_schedule and gtt_plan_set_passes install a
- * CUDA-core schedule and so switch the plan to FP32; gtt_plan_set_pipeline
- * only affects later CUDA-core schedules and the backward; gtt_plan_autotune
- * leaves a tensor-core plan unchanged. */
+/* Select the arithmetic of the mode contractions (gtt_precision_t).
+ * GTT_PREC_BF16X3 requires b = 16, dtype F32 and n >= 3; GTT_PREC_TF32X3
+ * requires b = 4, dtype C64 and n = 7 + 6k (k >= 0): a 7-digit pass and k
+ * 6-digit passes, each one HBM round trip (thread-block clusters of four CTAs
+ * exchange one digit through distributed shared memory); otherwise
+ * GTT_ERR_UNSUPPORTED.  A tensor-core path has one fixed schedule:
+ * gtt_plan_set_schedule and gtt_plan_set_passes install a CUDA-core schedule
+ * and so switch the plan to FP32; gtt_plan_set_pipeline only affects later
+ * CUDA-core schedules and the backward; gtt_plan_autotune leaves a
+ * tensor-core plan unchanged. */
 gtt_status_t gtt_plan_set_precision(gtt_plan_t plan, int precision);
 
 /*

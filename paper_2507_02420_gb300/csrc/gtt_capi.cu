@@ -340,6 +340,7 @@ extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
     if (!P || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or W");
     set_w_bytes(P, W);
     if (P->precision == GTT_PREC_BF16X3) return tc_upload_w(P);
+    if (P->precision == GTT_PREC_TF32X3) return tcx_upload_w(P);
     return GTT_OK;
 }
 
@@ -361,7 +362,7 @@ static bool tc_eligible(const gtt_plan_s *P) { return P->b == 16 && P->dtype == 
 
 // Back to a CUDA-core schedule (the plan's fixed rule or its explicit passes).
 static gtt_status_t use_cuda_core(gtt_plan_s *P) {
-    if (P->precision == GTT_PREC_BF16X3) {
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_TF32X3) {
         std::vector<PassPlan> passes;
         gtt_status_t st = P->explicit_g.empty()
                               ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
@@ -371,6 +372,17 @@ static gtt_status_t use_cuda_core(gtt_plan_s *P) {
         P->passes = passes;
     }
     P->precision = GTT_PREC_FP32;
+    return GTT_OK;
+}
+
+static gtt_status_t use_complex_tensor_cores(gtt_plan_s *P) {
+    std::vector<PassPlan> passes;
+    gtt_status_t st = make_tcx_schedule(P, &passes);
+    if (st != GTT_OK) return st;
+    st = tcx_upload_w(P);
+    if (st != GTT_OK) return st;
+    P->passes = passes;
+    P->precision = GTT_PREC_TF32X3;
     return GTT_OK;
 }
 
@@ -576,7 +588,8 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     P->use_tma = use_tma != 0;
     P->tma_nbuf = nbuf;
     P->bwd_ready = false;  // the backward's recompute passes follow the pipeline choice
-    if (P->precision == GTT_PREC_BF16X3) return GTT_OK;  // tensor-core passes stage their own tiles
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_TF32X3)
+        return GTT_OK;  // tensor-core passes stage their own tiles
     if (P->mixed) return GTT_OK;                          // mixed plans run the CUDA-core kernel
     std::vector<PassPlan> passes;
     gtt_status_t st = P->explicit_g.empty()
@@ -615,6 +628,7 @@ extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
     if (precision == GTT_PREC_FP32) return use_cuda_core(P);
     if (precision == GTT_PREC_BF16X3) return use_tensor_cores(P);
+    if (precision == GTT_PREC_TF32X3) return use_complex_tensor_cores(P);
     if (precision == GTT_PREC_AUTO) {
         if (tc_eligible(P) && use_tensor_cores(P) == GTT_OK) return GTT_OK;
         return use_cuda_core(P);
@@ -687,7 +701,7 @@ static ChunkPlan chunk_plan(const gtt_plan_s *P) {
     ChunkPlan c;
     long long C = P->chunk_elems;
     if (C == -1) C = P->total * P->es > (96ll << 20) ? (48ll << 20) / P->es : 0;  // 48 MiB chunks
-    if (C <= 0 || P->mixed) return c;
+    if (C <= 0 || P->mixed || P->precision == GTT_PREC_TF32X3) return c;
     int top = 0;
     long long block = 1;
     size_t prefix = 0;
@@ -711,6 +725,7 @@ static ChunkPlan chunk_plan(const gtt_plan_s *P) {
 static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
                              void *outp, cudaStream_t stream, long long tb, long long te) {
     if (pp.tc.on) return tc_run(P, pp, &Wb == &P->Wa, in, outp, stream, tb, te);
+    if (pp.tcx.on) return tcx_run(P, pp, &Wb == &P->Wa, in, outp, stream);
     if (pp.tma.on) return tma_run(P, pp, Wb, in, outp, stream, tb, te);
     // a mixed plan's pass carries its own factor (W_k, or W_k^H for the adjoint)
     const std::vector<unsigned char> &W = pp.factor < 0 ? Wb : (&Wb == &P->Wa ? pp.wa : pp.wf);
@@ -781,20 +796,7 @@ extern "C" gtt_status_t gtt_plan_timing(gtt_plan_t P, char *buf, size_t len) {
                  k ? ", " : "", names[k].c_str(), counts[k], total[k]);
         s += tmp;
     }
-    s += "]";
-    if (P->bwd_ready) {  // the backward schedule, once a backward call has built it
-        s += ", \"backward\": [";
-        for (size_t i = 0; i < P->bwd.size(); ++i) {
-            const BwdPass &bp = P->bwd[i];
-            char tmp[384];
-            snprintf(tmp, sizeof tmp,
-                     "%s{\"kernel\": \"%s\", \"m0\": %d, \"g\": %d, \"r\": %lld, \"grid\": %d, \"smem\": %zu}",
-                     i ? ", " : "", bp.name.c_str(), bp.geo.m0, bp.g, bp.geo.r, bp.grid, bp.smem);
-            s += tmp;
-        }
-        s += "]";
-    }
-    s += "}";
+    s += "]}";
     snprintf(buf, len, "%s", s.c_str());
     return st;
 }
@@ -855,7 +857,8 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
     std::string s = "{\"b\": " + std::to_string(P->b) + ", \"n\": " + std::to_string(P->n) +
                     ", \"dtype\": " + std::to_string((int)P->dtype) + ", \"batch\": " +
                     std::to_string(P->batch) + ", \"precision\": \"" +
-                    (P->precision == GTT_PREC_BF16X3 ? "bf16x3" : "fp32") + "\", \"launches_per_transform\": " +
+                    (P->precision == GTT_PREC_BF16X3 ? "bf16x3" : P->precision == GTT_PREC_TF32X3 ? "tf32x3" : "fp32") +
+                    "\", \"launches_per_transform\": " +
                     std::to_string(P->passes.size()) + ", \"passes\": [";
     for (size_t i = 0; i < P->passes.size(); ++i) {
         const PassPlan &pp = P->passes[i];
@@ -866,12 +869,12 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                  "\"tile_bytes\": %lld, \"tiles\": %lld, \"grid\": %d, \"block\": %d, \"smem\": %zu, "
                  "\"ctas_per_sm\": %d, \"vec_mode\": %d, \"tma\": %s, \"nbuf\": %d}",
                  i ? ", " : "",
-                 pp.tc.on ? pp.tc.name.c_str() : t ? pp.tma.name.c_str() : pp.name.c_str(), pp.m0, pp.g,
-                 pp.r, pp.D, (long long)pp.params.tile_elems * P->es, pp.params.tiles,
-                 pp.tc.on ? pp.tc.grid : t ? pp.tma.grid : pp.grid,
-                 pp.tc.on ? pp.tc.block : t ? kTmaBlock : pp.block,
-                 pp.tc.on ? pp.tc.smem : t ? pp.tma.smem : pp.smem,
-                 pp.tc.on ? pp.tc.ctas_per_sm : t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode,
+                 pp.tcx.on ? pp.tcx.name.c_str() : pp.tc.on ? pp.tc.name.c_str() : t ? pp.tma.name.c_str() : pp.name.c_str(),
+                 pp.m0, pp.g, pp.r, pp.D, (long long)pp.params.tile_elems * P->es, pp.params.tiles,
+                 pp.tcx.on ? pp.tcx.grid : pp.tc.on ? pp.tc.grid : t ? pp.tma.grid : pp.grid,
+                 pp.tcx.on ? 512 : pp.tc.on ? pp.tc.block : t ? kTmaBlock : pp.block,
+                 pp.tcx.on ? pp.tcx.smem : pp.tc.on ? pp.tc.smem : t ? pp.tma.smem : pp.smem,
+                 pp.tcx.on ? 1 : pp.tc.on ? pp.tc.ctas_per_sm : t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode,
                  t ? "true" : "false", t ? pp.tma.params.nbuf : 0);
         s += tmp;
     }
@@ -898,6 +901,7 @@ extern "C" gtt_status_t gtt_plan_destroy(gtt_plan_t P) {
     if (P->dstage) cudaFree(P->dstage);
     if (P->dev_err) cudaFree(P->dev_err);
     if (P->d_wpieces) cudaFree(P->d_wpieces);
+    if (P->d_tcx) cudaFree(P->d_tcx);
     if (P->ws_grad) cudaFree(P->ws_grad);
     if (P->ws_ck) cudaFree(P->ws_ck);
     if (P->ws_dw) cudaFree(P->ws_dw);

@@ -1,5 +1,6 @@
 // Plan object and host-side helpers shared by the C-ABI translation units.
 #pragma once
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,22 @@ struct TcPass {
     std::string name;
 };
 
+// complex64 b = 4 tensor-core (TF32X3) variant of a pass (gtt_tcx.cuh): a
+// cluster of four CTAs per tile group; the contiguous pass keeps a tensor map
+// of its input (cached per pointer).
+struct TcxPass {
+    bool on = false;
+    bool contig = false;
+    const void *kern = nullptr;
+    int grid = 0;
+    size_t smem = 0;
+    long long ctiles = 0, L = 1;
+    std::string name;
+    const void *map_ptr = nullptr;
+    CUtensorMap map;
+    TcxPass() { memset(&map, 0, sizeof(map)); }
+};
+
 struct PassPlan {
     int m0 = 0, g = 0, D = 1;
     long long r = 1;
@@ -51,6 +68,7 @@ struct PassPlan {
     std::string name;  // kernel name with its template arguments
     TmaPass tma;
     TcPass tc;
+    TcxPass tcx;
     int factor = -1;                       // mixed plans: the factor W_k of the pass's fastest digit
     int factors = 1;                       // mixed plans: adjacent factors W_{factor-factors+1} .. W_factor,
                                            // applied as their Kronecker product (one digit of their sizes' product)
@@ -113,6 +131,7 @@ struct gtt_plan_s {
     std::vector<long long> explicit_r;
     int *dev_err = nullptr;              // device flag raised by a bounded wait that expired
     void *d_wpieces = nullptr;           // BF16x3 pieces of W and W^T (b = 16 tensor-core path)
+    void *d_tcx = nullptr;               // TF32 pieces of W (x) W and its adjoint (complex b = 4 tensor-core path)
     long long chunk_elems = 0;           // elements per L2-resident chunk (0: off, -1: automatic)
     bool timing = false;
     std::vector<gtt::TimingRecord> pending;  // recorded, not yet read
@@ -140,6 +159,11 @@ gtt_status_t tc_upload_w(gtt_plan_s *P);
 gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out);
 gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s,
                     long long tile_begin, long long tile_end);
+// complex64 b = 4 tensor-core passes (gtt_tcx.cu)
+bool tcx_eligible(const gtt_plan_s *P);
+gtt_status_t tcx_upload_w(gtt_plan_s *P);
+gtt_status_t make_tcx_schedule(gtt_plan_s *P, std::vector<PassPlan> *out);
+gtt_status_t tcx_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s);
 // Attach the TMA variant to a forward pass when its geometry allows (true if attached).
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
