@@ -538,7 +538,8 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
     n2 = x2d.numel()
     res = {}
     outs = {}
-    for name, prec in (("fp32_cuda_core", g.PREC_FP32), ("bf16x3_tcgen05", g.PREC_BF16X3)):
+    for name, prec in (("fp32_cuda_core", g.PREC_FP32), ("bf16x3_tcgen05", g.PREC_BF16X3),
+                       ("bf16x2_tcgen05", g.PREC_BF16X2)):
         p2 = g.Plan(W2, 6, "f32", batch)
         p2.set_precision(prec)
         y2d = torch.empty_like(x2d)
@@ -563,12 +564,39 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
         oracle_check(res[name], "rel_l2_vs_oracle",
                      lambda yi=y_items: rel_l2(yi, oracle_modes(W2, x_items)))
         res[name]["oracle_items"] = items
-        res[name]["tolerance"] = 1e-6
+        res[name]["tolerance"] = 1e-6 if name != "bf16x2_tcgen05" else None
     best = lambda k: min(v["ms"] for kk, v in res.items() if kk.startswith(k))  # noqa: E731
     res["bf16x3_speedup_over_fp32"] = best("fp32_cuda_core") / best("bf16x3_tcgen05")
+    res["bf16x2_note"] = ("two-piece split, three products: about 2^-16 relative per mode; "
+                          "reported beside the three-piece/six-product path, not claimed against 1e-6")
+    res["tc_fp32_accumulation"] = tc_accumulation(g)
     del x2d, outs, y64, p64
     torch.cuda.empty_cache()
     return res
+
+
+def tc_accumulation(g):
+    """The tensor core's FP32 accumulation, measured through the library: b = 16,
+    n = 3, W = all ones (exact in BF16), and a single nonzero fibre of
+    BF16-exact values, so every output is the tensor core's FP32 sum of the 16
+    products of one MMA.  Three cases: 2^24 + 1.5 (rounding), and 1 with fifteen
+    2^-25 after or before it (width and order of the running sum)."""
+    import torch
+    W = np.ones((16, 16), dtype=np.float32)
+    cases = {"2^24 + 1.5": [2.0 ** 24, 1.5] + [0.0] * 14,
+             "1 then 15 x 2^-25": [1.0] + [2.0 ** -25] * 15,
+             "15 x 2^-25 then 1": [2.0 ** -25] * 15 + [1.0]}
+    plan = g.Plan(W, 3, "f32", 1)
+    plan.set_precision(g.PREC_BF16X3)
+    out = {}
+    for name, vals in cases.items():
+        x = np.zeros((16, 16, 16), dtype=np.float32)
+        x[0, 0, :] = np.asarray(vals, dtype=np.float32)
+        y = plan.forward(torch.from_numpy(x.reshape(1, -1)).cuda()).cpu().numpy()
+        out[name] = {"result": float(y[0, 0]), "minus_exact": float(np.float64(y[0, 0]) - float(np.sum(np.float64(vals))))}
+    out["reading"] = ("2^24 + 1.5 -> 2^24 + 2 is round-to-nearest, 2^24 truncation; 1.0 for the small terms means "
+                      "each product is rounded into an FP32 running sum")
+    return out
 
 
 def _fma_per_s() -> float:

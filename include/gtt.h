@@ -70,6 +70,10 @@ typedef enum {
                             n >= 3 (faster, and at least as accurate), else FP32      */
     GTT_PREC_FP32 = 1,   /* FP32 FMA on CUDA cores                                  */
     GTT_PREC_BF16X3 = 2, /* tcgen05 BF16 products of 3-piece splits, FP32 accumulate */
+    GTT_PREC_BF16X2 = 4, /* b = 16 FP32, opt-in: tcgen05 BF16 products of 2-piece
+                            splits (x0 W0 + x0 W1 + x1 W0), about 2^-16 relative
+                            per mode; the cheaper reading of split BF16, kept to
+                            compare with BF16X3                                     */
     GTT_PREC_TF32X3 = 3  /* complex64, b = 4, opt-in: pairs of digits as one base-16
                             digit with W (x) W, tcgen05 TF32 products of 2-piece
                             splits (three products), FP32 accumulate; the digits
@@ -126,7 +130,7 @@ gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int *radices, c
 gtt_status_t gtt_plan_set_w(gtt_plan_t plan, const void *W);
 
 /* Select the arithmetic of the mode contractions (gtt_precision_t).
- * GTT_PREC_BF16X3 requires b = 16, dtype F32 and n >= 3; GTT_PREC_TF32X3
+ * GTT_PREC_BF16X3 and GTT_PREC_BF16X2 require b = 16, dtype F32 and n >= 3; GTT_PREC_TF32X3
  * requires b = 4, dtype C64 and n = 7 + 6k (k >= 0): a 7-digit pass and k
  * 6-digit passes, each one HBM round trip (thread-block clusters of four CTAs
  * exchange one digit through distributed shared memory); otherwise

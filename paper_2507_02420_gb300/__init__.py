@@ -5,7 +5,7 @@ Sec. 3 of arXiv 2507.02420), in the paper's natural index ordering.  The
 computation runs in hand-written CUDA kernels behind the C ABI of
 include/gtt.h (libgtt.so); this package is its thin Python binding.
 """
-from .api import (C64, C128, F32, F64, I32, PREC_AUTO, PREC_BF16X3, PREC_FP32, PREC_TF32X3, Plan,  # noqa: F401
+from .api import (C64, C128, F32, F64, I32, PREC_AUTO, PREC_BF16X2, PREC_BF16X3, PREC_FP32, PREC_TF32X3, Plan,  # noqa: F401
                   dtype_code)
 from ._lib import GTTError, LIB_PATH, load  # noqa: F401
 from .autograd import GTTFunction, gtt  # noqa: F401

@@ -10,7 +10,12 @@ import ctypes
 import os
 import threading
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgtt.so")
+_HERE = os.path.dirname(os.path.abspath(__file__))
+# GTT_LIBRARY=debug loads the debug build (libgtt_debug.so: the same kernels
+# with every tile and global index checked, violations reported through
+# gtt_plan_check / gtt_group_check); anything else the release build.
+DEBUG = os.environ.get("GTT_LIBRARY", "") == "debug"
+LIB_PATH = os.path.join(_HERE, "libgtt_debug.so" if DEBUG else "libgtt.so")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -64,7 +69,7 @@ def load() -> ctypes.CDLL:
             return _lib
         if not os.path.exists(LIB_PATH):
             raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
-                              "(python -m paper_2507_02420_gb300.build)")
+                              "(python -m paper_2507_02420_gb300.build" + (" --debug)" if DEBUG else ")"))
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

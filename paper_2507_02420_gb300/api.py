@@ -14,7 +14,7 @@ import torch
 from ._lib import check, load
 
 F64, F32, C64, C128, I32 = 0, 1, 2, 3, 4
-PREC_AUTO, PREC_FP32, PREC_BF16X3, PREC_TF32X3 = 0, 1, 2, 3
+PREC_AUTO, PREC_FP32, PREC_BF16X3, PREC_TF32X3, PREC_BF16X2 = 0, 1, 2, 3, 4
 
 _TORCH_DT = {F64: torch.float64, F32: torch.float32, C64: torch.complex64,
              C128: torch.complex128, I32: torch.int32}

@@ -3,6 +3,12 @@
 Each csrc/*.cu is compiled to an object under _build/ in parallel, then all
 objects are linked into paper_2507_02420_gb300/libgtt.so (CUDA runtime linked
 statically).  Objects are rebuilt only when a source or header is newer.
+
+build(debug=True) compiles the same sources with -DGTT_DEBUG into
+_build_debug/ and libgtt_debug.so: every tile and global index of the kernels
+is checked, and a violation is reported through the plan's status word
+(gtt_plan_check) instead of touching memory outside the buffer.  Loaded when
+GTT_LIBRARY=debug is set.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgtt.so")
+OBJDIR_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libgtt_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -36,14 +44,15 @@ def _headers_mtime() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def _compile(src: str, hdr_mtime: float, verbose: bool) -> tuple[str, bool]:
-    obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, hdr_mtime: float, verbose: bool, debug: bool = False) -> tuple[str, bool]:
+    objdir = OBJDIR_DEBUG if debug else OBJDIR
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
     if os.path.exists(obj):
         om = os.path.getmtime(obj)
         if om >= os.path.getmtime(src) and om >= hdr_mtime:
             return obj, False
     tmp = obj + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-c", src, "-o", tmp] + ARCH + CFLAGS
+    cmd = [nvcc(), "-c", src, "-o", tmp] + ARCH + CFLAGS + (["-DGTT_DEBUG"] if debug else [])
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,28 +62,30 @@ def _compile(src: str, hdr_mtime: float, verbose: bool) -> tuple[str, bool]:
     return obj, True
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile and link libgtt.so; returns its path."""
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile and link libgtt.so (or libgtt_debug.so); returns its path."""
+    objdir, lib = (OBJDIR_DEBUG, LIB_DEBUG) if debug else (OBJDIR, LIB)
+    os.makedirs(objdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hm = _headers_mtime()
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, hm, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, hm, verbose, debug), srcs))
     objs = [o for o, _ in results]
     changed = any(c for _, c in results)
-    if changed or not os.path.exists(LIB) or \
-            os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if changed or not os.path.exists(lib) or \
+            os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    import sys
+    print(build(verbose=True, debug="--debug" in sys.argv[1:]))

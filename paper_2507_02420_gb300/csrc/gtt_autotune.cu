@@ -328,7 +328,7 @@ extern "C" gtt_status_t gtt_plan_autotune(gtt_plan_t P, int max_candidates) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device)
         return set_error(GTT_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");
-    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_TF32X3)
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2 || P->precision == GTT_PREC_TF32X3)
         return GTT_OK;  // a tensor-core path has one schedule
     return autotune(P, max_candidates > 0 ? max_candidates : 64);
 }

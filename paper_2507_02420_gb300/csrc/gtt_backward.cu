@@ -164,7 +164,9 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
     auto fwd_pass = [&](int q, const void *in, void *outp) -> gtt_status_t {
         PassPlan &fp = P->bwd[q].fwd;
         if (fp.tma.on) return tma_run(P, fp, Wf, in, outp, s, 0, fp.params.tiles);
-        void *args[4] = {(void *)&in, (void *)&outp, (void *)&fp.params, (void *)Wf.data()};
+        PassParams fpp = fp.params;
+        fpp.err = P->dev_err;
+        void *args[4] = {(void *)&in, (void *)&outp, (void *)&fpp, (void *)Wf.data()};
         return launch_timed(P, fp.kern, dim3(fp.grid), dim3(fp.block), args, fp.smem, s, fp.name);
     };
     // activations entering each backward pass, computed up front when they fit
@@ -196,8 +198,10 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
         void *Gout = GB;
         char *dwp = (char *)P->ws_dw + part_off * P->b * P->b * P->es;
         int g = bp.g;
+        PassParams gp = bp.geo.params;
+        gp.err = P->dev_err;
         void *args[8] = {(void *)&A, (void *)&Gin, (void *)&Gout, (void *)&dwp,
-                         (void *)&bp.geo.params, (void *)&g, (void *)Wf.data(), (void *)Wa.data()};
+                         (void *)&gp, (void *)&g, (void *)Wf.data(), (void *)Wa.data()};
         st = launch_timed(P, bp.kern, dim3(bp.grid), dim3(kBwdThreads), args, bp.smem, s, bp.name);
         if (st != GTT_OK) return st;
         part_off += bp.grid;

@@ -80,7 +80,7 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
             const long long rstride = p.vec_mode == 1 ? 0 : p.L;
             for (uint32_t c = tid; c < tile / CE; c += nth) {
                 const uint32_t row = p.vec_mode == 1 ? 0u : p.div_cpr.div(c), cc = c - row * cpr;
-                const long long ga = base + (long long)row * rstride + cc * CE;
+                const long long ga = GTT_CHECKED(base + (long long)row * rstride + cc * CE, p.total - CE + 1, p.err);
                 T va[CE], vg[CE];
                 load16(act_in + ga, va);
                 load16(grad_out + ga, vg);
@@ -94,7 +94,7 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
         } else {
             for (uint32_t e = tid; e < tile; e += nth) {
                 const uint32_t row = p.div_r.div(e), col = e - row * r;
-                const long long ga = base + (long long)row * p.L + col;
+                const long long ga = GTT_CHECKED(base + (long long)row * p.L + col, p.total, p.err);
                 s[spos<B>(e)] = act_in[ga];
                 G[spos<B>(e)] = grad_out[ga];
             }
@@ -214,12 +214,12 @@ gtt_backward_pass_kernel(const T *act_in, const T *grad_out, T *grad_in, T *dw_p
                 T v[CE];
 #pragma unroll
                 for (int i = 0; i < CE; ++i) v[i] = G[spos<B>(e0 + i)];
-                store16(grad_in + base + (long long)row * rstride + cc * CE, v);
+                store16(grad_in + GTT_CHECKED(base + (long long)row * rstride + cc * CE, p.total - CE + 1, p.err), v);
             }
         } else {
             for (uint32_t e = tid; e < tile; e += nth) {
                 const uint32_t row = p.div_r.div(e), col = e - row * r;
-                grad_in[base + (long long)row * p.L + col] = G[spos<B>(e)];
+                grad_in[GTT_CHECKED(base + (long long)row * p.L + col, p.total, p.err)] = G[spos<B>(e)];
             }
         }
         __syncthreads();

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gtt.h"
 #include "gtt_internal.h"
 #include "gtt_plan.h"
@@ -339,7 +341,7 @@ static void set_w_bytes(gtt_plan_s *P, const void *W) {
 extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
     if (!P || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or W");
     set_w_bytes(P, W);
-    if (P->precision == GTT_PREC_BF16X3) return tc_upload_w(P);
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2) return tc_upload_w(P);
     if (P->precision == GTT_PREC_TF32X3) return tcx_upload_w(P);
     return GTT_OK;
 }
@@ -362,7 +364,7 @@ static bool tc_eligible(const gtt_plan_s *P) { return P->b == 16 && P->dtype == 
 
 // Back to a CUDA-core schedule (the plan's fixed rule or its explicit passes).
 static gtt_status_t use_cuda_core(gtt_plan_s *P) {
-    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_TF32X3) {
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2 || P->precision == GTT_PREC_TF32X3) {
         std::vector<PassPlan> passes;
         gtt_status_t st = P->explicit_g.empty()
                               ? make_schedule(P, P->sched_tile_bytes, P->sched_run_bytes, &passes)
@@ -386,19 +388,28 @@ static gtt_status_t use_complex_tensor_cores(gtt_plan_s *P) {
     return GTT_OK;
 }
 
-static gtt_status_t use_tensor_cores(gtt_plan_s *P) {
+static gtt_status_t use_tensor_cores(gtt_plan_s *P, int np = 3) {
     std::vector<PassPlan> passes;
-    gtt_status_t st = make_tc_schedule(P, &passes);
+    gtt_status_t st = make_tc_schedule(P, np, &passes);
     if (st != GTT_OK) return st;
     st = tc_upload_w(P);
     if (st != GTT_OK) return st;
     P->passes = passes;
-    P->precision = GTT_PREC_BF16X3;
+    P->precision = np == 3 ? GTT_PREC_BF16X3 : GTT_PREC_BF16X2;
     return GTT_OK;
 }
 
+static gtt_status_t plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_dtype_t dtype, long long batch);
+
 extern "C" gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W,
                                         gtt_dtype_t dtype, long long batch) {
+    nvtxRangePushA("gtt_plan_create");
+    const gtt_status_t st = plan_create(out, b, n, W, dtype, batch);
+    nvtxRangePop();
+    return st;
+}
+
+static gtt_status_t plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_dtype_t dtype, long long batch) {
     if (!out || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL out or W");
     *out = nullptr;
     if (b < 2 || b > 16) return set_error(GTT_ERR_INVALID_ARG, "b must be in [2, 16]");
@@ -588,7 +599,7 @@ extern "C" gtt_status_t gtt_plan_set_pipeline(gtt_plan_t P, int use_tma, int nbu
     P->use_tma = use_tma != 0;
     P->tma_nbuf = nbuf;
     P->bwd_ready = false;  // the backward's recompute passes follow the pipeline choice
-    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_TF32X3)
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2 || P->precision == GTT_PREC_TF32X3)
         return GTT_OK;  // tensor-core passes stage their own tiles
     if (P->mixed) return GTT_OK;                          // mixed plans run the CUDA-core kernel
     std::vector<PassPlan> passes;
@@ -619,7 +630,8 @@ extern "C" gtt_status_t gtt_plan_check(gtt_plan_t P) {
     if (e != cudaSuccess) return cuda_error(e, "reading the error flag");
     if (flag) {
         cudaMemset(P->dev_err, 0, sizeof(int));
-        return set_error(GTT_ERR_TIMEOUT, "a bounded device-side wait expired in a TMA pass");
+        if (flag & 2) return set_error(GTT_ERR_INTERNAL, "an index check of the debug build failed in a kernel of this plan");
+        return set_error(GTT_ERR_TIMEOUT, "a bounded device-side wait expired in a kernel of this plan");
     }
     return GTT_OK;
 }
@@ -627,7 +639,8 @@ extern "C" gtt_status_t gtt_plan_check(gtt_plan_t P) {
 extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
     if (precision == GTT_PREC_FP32) return use_cuda_core(P);
-    if (precision == GTT_PREC_BF16X3) return use_tensor_cores(P);
+    if (precision == GTT_PREC_BF16X3) return use_tensor_cores(P, 3);
+    if (precision == GTT_PREC_BF16X2) return use_tensor_cores(P, 2);
     if (precision == GTT_PREC_TF32X3) return use_complex_tensor_cores(P);
     if (precision == GTT_PREC_AUTO) {
         if (tc_eligible(P) && use_tensor_cores(P) == GTT_OK) return GTT_OK;
@@ -674,7 +687,9 @@ gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block
         if (e == cudaSuccess) e = cudaEventRecord(rec.start, stream);
         if (e != cudaSuccess) return cuda_error(e, "timing event");
     }
+    nvtxRangePushA(name.c_str());  // a named range per launch (no cost unless a profiler listens)
     cudaError_t e = cudaLaunchKernel(kern, grid, block, args, smem, stream);
+    nvtxRangePop();
     if (e != cudaSuccess) return cuda_error(e, "kernel launch");
     if (P->timing) {
         e = cudaEventRecord(rec.stop, stream);
@@ -732,6 +747,7 @@ static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsi
     PassParams prm = pp.params;
     prm.tile_begin = tb;
     prm.tiles = te;
+    prm.err = P->dev_err;
     const int grid = (int)std::min<long long>(pp.grid, te - tb);
     void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)W.data()};
     return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
@@ -857,7 +873,10 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
     std::string s = "{\"b\": " + std::to_string(P->b) + ", \"n\": " + std::to_string(P->n) +
                     ", \"dtype\": " + std::to_string((int)P->dtype) + ", \"batch\": " +
                     std::to_string(P->batch) + ", \"precision\": \"" +
-                    (P->precision == GTT_PREC_BF16X3 ? "bf16x3" : P->precision == GTT_PREC_TF32X3 ? "tf32x3" : "fp32") +
+                    (P->precision == GTT_PREC_BF16X3   ? "bf16x3"
+                     : P->precision == GTT_PREC_BF16X2 ? "bf16x2"
+                     : P->precision == GTT_PREC_TF32X3 ? "tf32x3"
+                                                       : "fp32") +
                     "\", \"launches_per_transform\": " +
                     std::to_string(P->passes.size()) + ", \"passes\": [";
     for (size_t i = 0; i < P->passes.size(); ++i) {

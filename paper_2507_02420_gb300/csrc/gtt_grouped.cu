@@ -164,6 +164,8 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
     if (e == cudaSuccess) e = cudaMalloc(&G->d_counters, G->counter_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&G->d_err, sizeof(int));
     if (e != cudaSuccess) return fail(G, set_error(GTT_ERR_ALLOC, "group device tables"));
+    for (GroupReq &gr : hreqs)
+        for (int k = 0; k < gr.npass; ++k) gr.pass[k].p.err = G->d_err;  // status word of the debug build's checks
     e = cudaMemcpy(G->d_reqs, hreqs.data(), hreqs.size() * sizeof(GroupReq), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G->d_segs, segs.data(), segs.size() * sizeof(GroupSeg), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -237,6 +239,7 @@ extern "C" gtt_status_t gtt_group_check(gtt_group_t G) {
     if (e != cudaSuccess) return cuda_error(e, "reading the group error flag");
     if (flag) {
         cudaMemset(G->d_err, 0, sizeof(int));
+        if (flag & 2) return set_error(GTT_ERR_INTERNAL, "an index check of the debug build failed in the grouped kernel");
         return set_error(GTT_ERR_TIMEOUT, "a bounded wait between passes expired in the grouped kernel");
     }
     return GTT_OK;

@@ -120,7 +120,8 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
 #pragma unroll 4
         for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
             const uint32_t row = vec_mode == 1 ? 0u : div_cpr.div(c), cc = c - row * cpr;
-            const int4 raw = __ldcg(reinterpret_cast<const int4 *>(in + base + (long long)row * rstride + cc * CE));
+            const int4 raw = __ldcg(reinterpret_cast<const int4 *>(
+                in + GTT_CHECKED(base + (long long)row * rstride + cc * CE, p.total - CE + 1, p.err)));
             const T *v = reinterpret_cast<const T *>(&raw);
             const uint32_t e0 = vec_mode == 1 ? c * CE : row * r + cc * CE;
 #pragma unroll
@@ -145,7 +146,7 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
 #pragma unroll 4
         for (uint32_t e = tid; e < tile_elems; e += nth) {
             const uint32_t row = div_r.div(e), col = e - row * r;
-            s[spos<RB>(e)] = ld_cg(in + base + (long long)row * L + col);
+            s[spos<RB>(e)] = ld_cg(in + GTT_CHECKED(base + (long long)row * L + col, p.total, p.err));
         }
     }
     __syncthreads();
@@ -178,7 +179,7 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
             T v[CE];
 #pragma unroll
             for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(e0 + i)];
-            store16(out + base + (long long)row * rstride + cc * CE, v);
+            store16(out + GTT_CHECKED(base + (long long)row * rstride + cc * CE, p.total - CE + 1, p.err), v);
         }
     } else if (L == (long long)r) {  // contiguous, not in whole chunks: as the load
         T *dst = out + base;

@@ -95,7 +95,9 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
             if (fp.tma.on) {
                 st = tma_run(P, fp, Wf, in, outp, s, 0, fp.params.tiles);
             } else {
-                void *args[4] = {(void *)&in, (void *)&outp, (void *)&fp.params, (void *)Wf.data()};
+                PassParams fpp = fp.params;
+                fpp.err = P->dev_err;
+                void *args[4] = {(void *)&in, (void *)&outp, (void *)&fpp, (void *)Wf.data()};
                 st = launch_timed(P, fp.kern, dim3(fp.grid), dim3(fp.block), args, fp.smem, s, fp.name);
             }
             if (st != GTT_OK) return st;
@@ -105,8 +107,10 @@ extern "C" gtt_status_t gtt_backward_noalloc(gtt_plan_t P, const void *x, const 
         void *Gout = dx;
         char *dwp = (char *)scratch + part_off * P->b * P->b * P->es;
         int g = bp.g;
+        PassParams gp = bp.geo.params;
+        gp.err = P->dev_err;
         void *args[8] = {(void *)&A, (void *)&Gin, (void *)&Gout, (void *)&dwp,
-                         (void *)&bp.geo.params, (void *)&g, (void *)Wf.data(), (void *)Wa.data()};
+                         (void *)&gp, (void *)&g, (void *)Wf.data(), (void *)Wa.data()};
         st = launch_timed(P, bp.kern, dim3(bp.grid), dim3(kBwdThreads), args, bp.smem, s, bp.name);
         if (st != GTT_OK) return st;
         part_off += bp.grid;

@@ -48,6 +48,7 @@ struct PassParams {
     int stage_mask[kMaxStages];  // bit k set: apply W to window digit k in this stage
     uint32_t stage_strideA[kMaxStages];  // r * b^a
     FastDiv stage_divBa[kMaxStages];     // division by b^a
+    int *err;             // the plan's status word (bounds checks of the debug build)
 };
 
 // smem position of tile element e: one pad element after every B^D elements,
@@ -151,6 +152,10 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
     constexpr int CE = Vec16<T>::n;  // elements per 16-byte chunk
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
+    // smem slot of tile element e (padded), and global element offsets, checked in the debug build
+    const uint32_t smem_elems = p.tile_elems + p.tile_elems / cpow(B, D) + 1;
+#define SP(e) GTT_CHECKED(spos<RB>(e), smem_elems, p.err)
+#define GI(off, w) GTT_CHECKED(off, p.total - base - (w) + 1, p.err)
 
     const uint32_t tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tile_elems = p.tile_elems, r = p.r;
@@ -166,18 +171,18 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
         if (p.vec_mode == 1) {  // contiguous tile, 16-byte chunks
             for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
                 T v[CE];
-                load16(gin + (size_t)c * CE, v);
+                load16(gin + GI((size_t)c * CE, CE), v);
 #pragma unroll
-                for (int i = 0; i < CE; ++i) s[spos<RB>(c * CE + i)] = v[i];
+                for (int i = 0; i < CE; ++i) s[SP(c * CE + i)] = v[i];
             }
         } else if (p.vec_mode == 2) {  // rows of r elements, r % CE == 0
             const uint32_t cpr = r / CE;
             for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
                 const uint32_t row = p.div_cpr.div(c), cc = c - row * cpr;
                 T v[CE];
-                load16(gin + (long long)row * p.L + cc * CE, v);
+                load16(gin + GI((long long)row * p.L + cc * CE, CE), v);
 #pragma unroll
-                for (int i = 0; i < CE; ++i) s[spos<RB>(row * r + cc * CE + i)] = v[i];
+                for (int i = 0; i < CE; ++i) s[SP(row * r + cc * CE + i)] = v[i];
             }
         } else if (p.L == (long long)r) {
             // contiguous, but not in whole 16-byte chunks (odd radices): the
@@ -185,18 +190,18 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
             // chunks, then the rest
             const uint32_t head = min(tile_elems, (uint32_t)((CE - ((uintptr_t)gin / sizeof(T)) % CE) % CE));
             const uint32_t nch = (tile_elems - head) / CE, mid_end = head + nch * CE;
-            for (uint32_t e = tid; e < head; e += nth) s[spos<RB>(e)] = gin[e];
+            for (uint32_t e = tid; e < head; e += nth) s[SP(e)] = gin[GI(e, 1)];
             for (uint32_t c = tid; c < nch; c += nth) {
                 T v[CE];
-                load16(gin + head + (size_t)c * CE, v);
+                load16(gin + GI(head + (size_t)c * CE, CE), v);
 #pragma unroll
-                for (int i = 0; i < CE; ++i) s[spos<RB>(head + c * CE + i)] = v[i];
+                for (int i = 0; i < CE; ++i) s[SP(head + c * CE + i)] = v[i];
             }
-            for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) s[spos<RB>(e)] = gin[e];
+            for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) s[SP(e)] = gin[GI(e, 1)];
         } else {
             for (uint32_t e = tid; e < tile_elems; e += nth) {
                 const uint32_t row = p.div_r.div(e), col = e - row * r;
-                s[spos<RB>(e)] = gin[(long long)row * p.L + col];
+                s[SP(e)] = gin[GI((long long)row * p.L + col, 1)];
             }
         }
         __syncthreads();
@@ -215,10 +220,10 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
                 const uint32_t e0 = high * (strideA * RB) + low * r + col;
                 T v[RB];
 #pragma unroll
-                for (int q = 0; q < RB; ++q) v[q] = s[spos<RB>(e0 + q * strideA)];
+                for (int q = 0; q < RB; ++q) v[q] = s[SP(e0 + q * strideA)];
                 apply_window<T, B, D>(v, mask, W);
 #pragma unroll
-                for (int q = 0; q < RB; ++q) s[spos<RB>(e0 + q * strideA)] = v[q];
+                for (int q = 0; q < RB; ++q) s[SP(e0 + q * strideA)] = v[q];
             }
             __syncthreads();
         }
@@ -229,8 +234,8 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
             for (uint32_t c = tid; c < tile_elems / CE; c += nth) {
                 T v[CE];
 #pragma unroll
-                for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(c * CE + i)];
-                store16(gout + (size_t)c * CE, v);
+                for (int i = 0; i < CE; ++i) v[i] = s[SP(c * CE + i)];
+                store16(gout + GI((size_t)c * CE, CE), v);
             }
         } else if (p.vec_mode == 2) {
             const uint32_t cpr = r / CE;
@@ -238,28 +243,30 @@ gtt_pass_kernel(const T *in, T *out, PassParams p, WMat<T, B> W) {
                 const uint32_t row = p.div_cpr.div(c), cc = c - row * cpr;
                 T v[CE];
 #pragma unroll
-                for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(row * r + cc * CE + i)];
-                store16(gout + (long long)row * p.L + cc * CE, v);
+                for (int i = 0; i < CE; ++i) v[i] = s[SP(row * r + cc * CE + i)];
+                store16(gout + GI((long long)row * p.L + cc * CE, CE), v);
             }
         } else if (p.L == (long long)r) {  // contiguous, not in whole chunks: as the load
             const uint32_t head = min(tile_elems, (uint32_t)((CE - ((uintptr_t)gout / sizeof(T)) % CE) % CE));
             const uint32_t nch = (tile_elems - head) / CE, mid_end = head + nch * CE;
-            for (uint32_t e = tid; e < head; e += nth) gout[e] = s[spos<RB>(e)];
+            for (uint32_t e = tid; e < head; e += nth) gout[GI(e, 1)] = s[SP(e)];
             for (uint32_t c = tid; c < nch; c += nth) {
                 T v[CE];
 #pragma unroll
-                for (int i = 0; i < CE; ++i) v[i] = s[spos<RB>(head + c * CE + i)];
-                store16(gout + head + (size_t)c * CE, v);
+                for (int i = 0; i < CE; ++i) v[i] = s[SP(head + c * CE + i)];
+                store16(gout + GI(head + (size_t)c * CE, CE), v);
             }
-            for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) gout[e] = s[spos<RB>(e)];
+            for (uint32_t e = mid_end + tid; e < tile_elems; e += nth) gout[GI(e, 1)] = s[SP(e)];
         } else {
             for (uint32_t e = tid; e < tile_elems; e += nth) {
                 const uint32_t row = p.div_r.div(e), col = e - row * r;
-                gout[(long long)row * p.L + col] = s[spos<RB>(e)];
+                gout[GI((long long)row * p.L + col, 1)] = s[SP(e)];
             }
         }
         __syncthreads();
     }
+#undef SP
+#undef GI
 }
 
 } // namespace gtt

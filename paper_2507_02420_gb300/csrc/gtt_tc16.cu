@@ -48,9 +48,12 @@ gtt_status_t tc_upload_w(gtt_plan_s *P) {
     return GTT_OK;
 }
 
-static const void *tc_kernel(int g) {
-    return g == 3 ? (const void *)&gtt_tc16_pass_kernel<3>
-                  : g == 2 ? (const void *)&gtt_tc16_pass_kernel<2> : (const void *)&gtt_tc16_pass_kernel<1>;
+static const void *tc_kernel(int g, int np) {
+    if (np == 2)
+        return g == 3 ? (const void *)&gtt_tc16_pass_kernel<3, 2>
+                      : g == 2 ? (const void *)&gtt_tc16_pass_kernel<2, 2> : (const void *)&gtt_tc16_pass_kernel<1, 2>;
+    return g == 3 ? (const void *)&gtt_tc16_pass_kernel<3, 3>
+                  : g == 2 ? (const void *)&gtt_tc16_pass_kernel<2, 3> : (const void *)&gtt_tc16_pass_kernel<1, 3>;
 }
 
 // CTAs of a tensor-core pass kernel per SM, from the register and shared-memory
@@ -72,16 +75,16 @@ static int tc_residency(gtt_plan_s *P, const void *k) {
 
 // Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (2, r=16)
 // passes, and a final (1, r=256) pass when one digit is left.
-gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
+gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out) {
     if (P->b != 16 || P->dtype != GTT_F32 || P->n < 3)
-        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 needs b = 16, FP32 and n >= 3");
+        return set_error(GTT_ERR_UNSUPPORTED, "BF16X3 and BF16X2 need b = 16, FP32 and n >= 3");
     std::vector<PassPlan> passes;
     int m0 = 0;
     while (m0 < P->n) {
         const int left = P->n - m0;
         const int g = m0 == 0 ? 3 : (left >= 2 ? 2 : 1);
         const long long r = m0 == 0 ? 1 : (g == 2 ? 16 : 256);
-        const void *k = tc_kernel(g);
+        const void *k = tc_kernel(g, np);
         const int per_sm = tc_residency(P, k);
         if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
         PassPlan pp;
@@ -94,7 +97,7 @@ gtt_status_t make_tc_schedule(gtt_plan_s *P, std::vector<PassPlan> *out) {
         pp.tc.ctas_per_sm = per_sm;
         pp.tc.block = kTcThreads;
         pp.tc.smem = kTcSmemPerCta;
-        pp.tc.name = "gtt_tc16_pass_kernel<bf16x3,g=" + std::to_string(g) + ">";
+        pp.tc.name = std::string("gtt_tc16_pass_kernel<") + (np == 3 ? "bf16x3" : "bf16x2") + ",g=" + std::to_string(g) + ">";
         passes.push_back(pp);
         m0 += g;
     }

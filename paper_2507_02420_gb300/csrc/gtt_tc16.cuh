@@ -16,6 +16,10 @@
 //   x0 . [W0|W1|W2] (N = 48), x1 . [W0|W1] (N = 32, into C1 C2), x2 . W0 (N = 16, into C2),
 // and y = (C2 + C1) + C0 on readback.  The dropped terms are below 2^-24
 // relative, so the result matches FP32 to within a few ulps.
+// The two-piece variant (NP = 2: x = x0 + x1, W = W0 + W1, products x0 W0,
+// x0 W1, x1 W0 into C0 and C1, y = C1 + C0) leaves the x residual and x1 W1,
+// about 2^-16 relative per mode: the cheaper, less accurate reading of "bf16x3"
+// (BF16X2 in the C ABI), kept for the precision comparison.
 //
 // Operands (shared memory, K-major, no swizzle): core matrices of 8 rows x 16
 // bytes, the two K-halves 128 bytes apart (leading byte offset) and 8-row
@@ -134,7 +138,7 @@ struct TcCtx {
 // (the A operand), run the BF16x3 MMAs into TMEM, and write y_m back to S
 // (D < 2) or, for the last mode, straight to global memory at o[n * stride_n].
 // Returns false in a thread whose wait for the MMA completion timed out.
-template <int D>
+template <int D, int NP>
 __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phase, float *o, long long stride_n) {
     uint32_t off[16];
     tc_fibre<D>(c.m, off);
@@ -172,7 +176,7 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
         const uint32_t ko = kmaj_off(c.m, 8 * h);
         *reinterpret_cast<uint4 *>(c.A + ko) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
         *reinterpret_cast<uint4 *>(c.A + kTcPieceBytes + ko) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-        *reinterpret_cast<uint4 *>(c.A + 2 * kTcPieceBytes + ko) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        if (NP == 3) *reinterpret_cast<uint4 *>(c.A + 2 * kTcPieceBytes + ko) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
     }
     fence_proxy_async();  // generic-proxy writes of A, visible to the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -183,9 +187,14 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
         for (uint32_t b2 = 0; b2 < 2; ++b2) {
             const uint32_t dcol = c.tmem + b2 * 64u;
             const uint32_t aoff = c.a_smem + b2 * 4096u;  // rows 128 b2 .. (16 groups x 256 B)
-            umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(48), 0u);
-            umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(32), 1u);
-            umma_bf16(dcol + 32u, umma_sdesc(aoff + 2 * kTcPieceBytes), c.descB, umma_idesc(16), 1u);
+            if (NP == 3) {
+                umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(48), 0u);
+                umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(32), 1u);
+                umma_bf16(dcol + 32u, umma_sdesc(aoff + 2 * kTcPieceBytes), c.descB, umma_idesc(16), 1u);
+            } else {
+                umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(32), 0u);
+                umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(16), 1u);
+            }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.bar)
                      : "memory");
@@ -198,13 +207,14 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
     float c0[16], c1[16], c2[16];
     tmem_ld16(c.tmem_row, c0);
     tmem_ld16(c.tmem_row + 16u, c1);
-    tmem_ld16(c.tmem_row + 32u, c2);
+    if (NP == 3) tmem_ld16(c.tmem_row + 32u, c2);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     float y[16];
 #pragma unroll
     for (int n = 0; n < 16; n += 2) {
-        const float2 s = __fadd2_rn(__fadd2_rn(make_float2(c2[n], c2[n + 1]), make_float2(c1[n], c1[n + 1])),
-                                    make_float2(c0[n], c0[n + 1]));
+        const float2 s = NP == 3 ? __fadd2_rn(__fadd2_rn(make_float2(c2[n], c2[n + 1]), make_float2(c1[n], c1[n + 1])),
+                                              make_float2(c0[n], c0[n + 1]))
+                                 : __fadd2_rn(make_float2(c1[n], c1[n + 1]), make_float2(c0[n], c0[n + 1]));
         y[n] = s.x, y[n + 1] = s.y;
     }
     if (D == 0) {
@@ -231,7 +241,7 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
 
 // Pass over tiles of three base-16 digits whose top G are transformed (G = 3:
 // contiguous tiles of the first pass; G = 2, 1: runs of r = 16, 256 elements).
-template <int G>
+template <int G, int NP>
 __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const float *in, float *out, TcParams tp) {
     constexpr uint32_t kLogR = 4u * (3u - G);  // run length r = 16^(3-G)
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -287,8 +297,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
             for (int i = 0; i < kTcTile / 4 / kTcThreads; ++i) {
                 const uint32_t cc = tid + (uint32_t)i * kTcThreads, e = cc * 4u;
                 const uint32_t row = e >> kLogR, col = e & ((1u << kLogR) - 1u);
-                const float *src = in + gb + (long long)row * p.L + col;
-                const uint32_t dst = smem_addr(Sb + tc_pos(cc >> 6, (cc >> 2) & 15u, (cc & 3u) * 4u));
+                const float *src = in + GTT_CHECKED(gb + (long long)row * p.L + col, p.total - 3, tp.err);
+                const uint32_t dst = smem_addr(Sb + GTT_CHECKED(tc_pos(cc >> 6, (cc >> 2) & 15u, (cc & 3u) * 4u), kTcTile - 3, tp.err));
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
             }
         }
@@ -310,9 +320,21 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
         }
         float *S = ring + slot * kTcTile;
         float *o = out + tile_base(t) + (long long)rowm * p.L + colm;
-        if (G == 3) bad |= !tc_mode<0>(c, S, phase, o, stride_n);
-        if (G >= 2) bad |= !tc_mode<1>(c, S, phase, o, stride_n);
-        bad |= !tc_mode<2>(c, S, phase, o, stride_n);
+#ifdef GTT_DEBUG
+        long long stride_o = stride_n;
+        if (tile_base(t) + (long long)rowm * p.L + colm + 15 * stride_n >= p.total) {  // last-mode stores stay inside
+            atomicOr(tp.err, 2);
+            o = out;
+            stride_o = 0;
+        }
+#define stride_n stride_o
+#endif
+        if (G == 3) bad |= !tc_mode<0, NP>(c, S, phase, o, stride_n);
+        if (G >= 2) bad |= !tc_mode<1, NP>(c, S, phase, o, stride_n);
+        bad |= !tc_mode<2, NP>(c, S, phase, o, stride_n);
+#ifdef GTT_DEBUG
+#undef stride_n
+#endif
         slot = slot == 2 ? 0 : slot + 1;
     }
     if (!failed && __syncthreads_or(bad)) failed = true;  // the last tile's vote

@@ -232,6 +232,7 @@ __device__ __forceinline__ void st_async16(uint32_t addr, float4 v, uint32_t bar
 struct TcxMode {
     uint32_t tmem, trow, colA0, colD, mma_bar, gi, tt;
     uint64_t bdesc;
+    int *err;  // the plan's status word (bounds checks of the debug build)
 };
 
 // Float offset, in a contiguous tile, of element kk of this thread's fibre in
@@ -274,8 +275,8 @@ __device__ __forceinline__ void tcx_mode_mma(const TcxMode &c, const float *S, f
         } else {
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
-                const float2 t =
-                    *reinterpret_cast<const float2 *>(S + (CONTIG ? contig_off<MODE>(c.tt, kk) : strided_off<MODE>(c.tt, kk)));
+                const float2 t = *reinterpret_cast<const float2 *>(
+                    S + GTT_CHECKED(CONTIG ? contig_off<MODE>(c.tt, kk) : strided_off<MODE>(c.tt, kk), 2 * kTcxTile - 1, c.err));
                 v[2 * kk] = t.x, v[2 * kk + 1] = t.y;
             }
         }
@@ -317,7 +318,8 @@ __device__ __forceinline__ void tcx_mode_mma(const TcxMode &c, const float *S, f
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 // Write y of this thread's fibre back to the tile (mode MODE's positions).
-template <bool CONTIG, int MODE> __device__ __forceinline__ void tcx_write_back(uint32_t tt, float *S, const float (&v)[32]) {
+template <bool CONTIG, int MODE>
+__device__ __forceinline__ void tcx_write_back(uint32_t tt, float *S, const float (&v)[32], int *err) {
     if (CONTIG && MODE == 0) {
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -326,8 +328,8 @@ template <bool CONTIG, int MODE> __device__ __forceinline__ void tcx_write_back(
     } else {
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk)
-            *reinterpret_cast<float2 *>(S + (CONTIG ? contig_off<MODE>(tt, kk) : strided_off<MODE>(tt, kk))) =
-                make_float2(v[2 * kk], v[2 * kk + 1]);
+            *reinterpret_cast<float2 *>(S + GTT_CHECKED(CONTIG ? contig_off<MODE>(tt, kk) : strided_off<MODE>(tt, kk),
+                                                        2 * kTcxTile - 1, err)) = make_float2(v[2 * kk], v[2 * kk + 1]);
     }
 }
 
@@ -436,6 +438,7 @@ gtt_tcx_pass_kernel(const __grid_constant__ CUtensorMap tin, const float2 *in, f
     mc.gi = gi;
     mc.tt = tt;
     mc.bdesc = tcx_bdesc(smem_addr(Bs));
+    mc.err = p.err;
     uint32_t mma_phase = 0;
 
     for (long long k = slot; k < my_tiles; k += kTcxSlots) {
@@ -456,10 +459,10 @@ gtt_tcx_pass_kernel(const __grid_constant__ CUtensorMap tin, const float2 *in, f
         float v[32];
         if constexpr (CONTIG) {
             tcx_mode_mma<true, 0>(mc, S, v, mma_phase, ok, abort_flag);
-            if (live()) tcx_write_back<true, 0>(tt, S, v);
+            if (live()) tcx_write_back<true, 0>(tt, S, v, p.err);
             slot_sync(slot);
             tcx_mode_mma<true, 1>(mc, S, v, mma_phase, ok, abort_flag);
-            if (live()) tcx_write_back<true, 1>(tt, S, v);
+            if (live()) tcx_write_back<true, 1>(tt, S, v, p.err);
             slot_sync(slot);
             tcx_mode_mma<true, 2>(mc, S, v, mma_phase, ok, abort_flag);
             wait_xfree();
@@ -475,10 +478,10 @@ gtt_tcx_pass_kernel(const __grid_constant__ CUtensorMap tin, const float2 *in, f
             }
         } else {
             tcx_mode_mma<false, 0>(mc, S, v, mma_phase, ok, abort_flag);
-            if (live()) tcx_write_back<false, 0>(tt, S, v);
+            if (live()) tcx_write_back<false, 0>(tt, S, v, p.err);
             slot_sync(slot);
             tcx_mode_mma<false, 1>(mc, S, v, mma_phase, ok, abort_flag);
-            if (live()) tcx_write_back<false, 1>(tt, S, v);
+            if (live()) tcx_write_back<false, 1>(tt, S, v, p.err);
             slot_sync(slot);
             // the base-4 digit of row bits 8-9 on CUDA cores; output row tt + 256 o goes to
             // CTA o as complex 4 tt .. 4 tt + 3 of our slot
@@ -542,12 +545,14 @@ gtt_tcx_pass_kernel(const __grid_constant__ CUtensorMap tin, const float2 *in, f
                 }
                 if constexpr (CONTIG) {
                     // complex j of the group: position m + 256 (4 rank + j) of tile o
-                    float2 *dst = out + ct * (long long)(4 * kTcxTile) + (long long)o * kTcxTile + 1024ll * rank + m;
+                    float2 *dst = out + GTT_CHECKED(ct * (long long)(4 * kTcxTile) + (long long)o * kTcxTile + 1024ll * rank + m,
+                                                    p.ctiles * 4 * kTcxTile - 768, p.err);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) dst[256 * j] = a[j];
                 } else {
                     // row 256 rank + m, columns 0..3, cluster digit o
-                    float2 *dst = out + strided_origin(ct, (uint32_t)o) + (long long)(256u * rank + m) * p.L;
+                    float2 *dst = out + GTT_CHECKED(strided_origin(ct, (uint32_t)o) + (long long)(256u * rank + m) * p.L,
+                                                    p.ctiles * 4 * kTcxTile - 3, p.err);
                     reinterpret_cast<float4 *>(dst)[0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
                     reinterpret_cast<float4 *>(dst)[1] = make_float4(a[2].x, a[2].y, a[3].x, a[3].y);
                 }

@@ -286,6 +286,8 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
                 break;
             }
             unsigned char *tb = sbase + (size_t)buf * p.tile_bytes;
+            // byte offset of an element of T in the tile, checked in the debug build
+#define TB(off) GTT_CHECKED(off, p.tile_bytes - sizeof(T) + 1, p.err)
 
             const uint32_t nslots = p.tile_elems / RB;
             for (int st = 0; st < p.nstages; ++st) {
@@ -303,11 +305,11 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
 #pragma unroll
                             for (int q = 0; q < RB; q += CE)
                                 *reinterpret_cast<int4 *>(&v[q]) =
-                                    *reinterpret_cast<const int4 *>(tb + Tile::off(row0 + q, 0, p.M));
+                                    *reinterpret_cast<const int4 *>(tb + GTT_CHECKED(Tile::off(row0 + q, 0, p.M), p.tile_bytes - 15, p.err));
                             apply_window<T, B, D>(v, mask, W);
 #pragma unroll
                             for (int q = 0; q < RB; q += CE)
-                                *reinterpret_cast<int4 *>(tb + Tile::off(row0 + q, 0, p.M)) =
+                                *reinterpret_cast<int4 *>(tb + GTT_CHECKED(Tile::off(row0 + q, 0, p.M), p.tile_bytes - 15, p.err)) =
                                     *reinterpret_cast<const int4 *>(&v[q]);
                             continue;
                         }
@@ -317,18 +319,18 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
                         const uint32_t a0 = Tile::off(row0, col, p.M);
                         const uint32_t *fq = p.stage_fq[st];
 #pragma unroll
-                        for (int q = 0; q < RB; ++q) v[q] = *reinterpret_cast<const T *>(tb + (a0 ^ fq[q]));
+                        for (int q = 0; q < RB; ++q) v[q] = *reinterpret_cast<const T *>(tb + TB(a0 ^ fq[q]));
                         apply_window<T, B, D>(v, mask, W);
 #pragma unroll
-                        for (int q = 0; q < RB; ++q) *reinterpret_cast<T *>(tb + (a0 ^ fq[q])) = v[q];
+                        for (int q = 0; q < RB; ++q) *reinterpret_cast<T *>(tb + TB(a0 ^ fq[q])) = v[q];
                     } else if (form == kAddrStride) {
                         unsigned char *a0 = tb + Tile::off(row0, col, p.M);
                         const uint32_t stride = p.stage_stride[st];
 #pragma unroll
-                        for (int q = 0; q < RB; ++q) v[q] = *reinterpret_cast<const T *>(a0 + q * stride);
+                        for (int q = 0; q < RB; ++q) v[q] = *reinterpret_cast<const T *>(tb + TB((a0 - tb) + q * stride));
                         apply_window<T, B, D>(v, mask, W);
 #pragma unroll
-                        for (int q = 0; q < RB; ++q) *reinterpret_cast<T *>(a0 + q * stride) = v[q];
+                        for (int q = 0; q < RB; ++q) *reinterpret_cast<T *>(tb + TB((a0 - tb) + q * stride)) = v[q];
                     } else if (form == kAddrRowXor) {
                         // swizzle row of element 0 (a multiple of 8) and its byte in the row
                         const uint32_t off0 = Tile::off(row0, col, p.M);  // chunk phase 0 at q = 0
@@ -336,23 +338,24 @@ gtt_tma_pass_kernel(const __grid_constant__ CUtensorMap tin, const __grid_consta
                         const uint32_t c = (off0 >> 4) & 7u;
 #pragma unroll
                         for (int q = 0; q < RB; ++q)
-                            v[q] = *reinterpret_cast<const T *>(rbase + q * 128 + (((c ^ (uint32_t)q) & 7u) << 4));
+                            v[q] = *reinterpret_cast<const T *>(tb + TB((rbase - tb) + q * 128 + (((c ^ (uint32_t)q) & 7u) << 4)));
                         apply_window<T, B, D>(v, mask, W);
 #pragma unroll
                         for (int q = 0; q < RB; ++q)
-                            *reinterpret_cast<T *>(rbase + q * 128 + (((c ^ (uint32_t)q) & 7u) << 4)) = v[q];
+                            *reinterpret_cast<T *>(tb + TB((rbase - tb) + q * 128 + (((c ^ (uint32_t)q) & 7u) << 4))) = v[q];
                     } else {
 #pragma unroll
                         for (int q = 0; q < RB; ++q)
-                            v[q] = *reinterpret_cast<const T *>(tb + Tile::off(row0 + q * Ba, col, p.M));
+                            v[q] = *reinterpret_cast<const T *>(tb + TB(Tile::off(row0 + q * Ba, col, p.M)));
                         apply_window<T, B, D>(v, mask, W);
 #pragma unroll
                         for (int q = 0; q < RB; ++q)
-                            *reinterpret_cast<T *>(tb + Tile::off(row0 + q * Ba, col, p.M)) = v[q];
+                            *reinterpret_cast<T *>(tb + TB(Tile::off(row0 + q * Ba, col, p.M))) = v[q];
                     }
                 }
                 if (st + 1 < p.nstages) compute_sync();
             }
+#undef TB
             fence_proxy_async();  // this thread's smem writes, visible to the TMA store
             mbar_arrive(empty + 8u * buf);
         }

@@ -84,6 +84,24 @@ __device__ __forceinline__ double add_(double a, double b) { return a + b; }
 __device__ __forceinline__ c64 add_(c64 a, c64 b) { return c64{a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ c128 add_(c128 a, c128 b) { return c128{a.re + b.re, a.im + b.im}; }
 
+// Index checks of the debug build (compiled with -DGTT_DEBUG into
+// libgtt_debug.so; the release library has none).  An index outside
+// [0, n) sets bit 1 (value 2) of the plan's status word and is replaced by 0,
+// a location inside the buffer, so the kernel goes on without touching memory
+// it does not own; gtt_plan_check reports the violation.  Nothing traps.
+#ifdef GTT_DEBUG
+__device__ __forceinline__ long long gtt_dbg_index(long long i, long long n, int *err) {
+    if (i < 0 || i >= n) {
+        if (err) atomicOr(err, 2);
+        return 0;
+    }
+    return i;
+}
+#define GTT_CHECKED(i, n, err) (::gtt::gtt_dbg_index((long long)(i), (long long)(n), (err)))
+#else
+#define GTT_CHECKED(i, n, err) (i)
+#endif
+
 // Compile-time integer power.
 __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 

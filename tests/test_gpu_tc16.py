@@ -137,3 +137,70 @@ def test_auto_precision_picks_tensor_cores_for_b16_fp32(g):
             assert plan.describe()["precision"] == "bf16x3"
             plan.set_schedule(16384, 128)        # a CUDA-core schedule: FP32
             assert plan.describe()["precision"] == "fp32"
+
+
+@pytest.mark.parametrize("n,batch", [(4, 2), (6, 1)])
+def test_bf16x2_two_piece_error_against_three_piece(g, n, batch):
+    """The two-piece split (three products) leaves about 2^-16 relative per
+    mode; the three-piece split (six products) reaches FP32 accuracy.  Both
+    measured against the FP64 oracle on the same input."""
+    rng = np.random.default_rng(9500 + n)
+    W = gi.haar_orthogonal(16, rng).astype(np.float32)
+    x = gi.normal_x((batch, 16 ** n), rng, np.float32)
+    xd = torch.from_numpy(x).cuda()
+    ref = oracle.modes(W.astype(np.float64), x.astype(np.float64))
+    errs = {}
+    for name, prec in (("bf16x2", g.PREC_BF16X2), ("bf16x3", g.PREC_BF16X3)):
+        plan = g.Plan(W, n, "f32", batch)
+        plan.set_precision(prec)
+        d = plan.describe()
+        assert d["precision"] == name and all(name in p["kernel"] for p in d["passes"]), d
+        errs[name] = rel(plan.forward(xd).cpu().numpy(), ref)
+        plan.check()
+    print(f"b=16 n={n}: bf16x2 rel-L2 {errs['bf16x2']:.3e}, bf16x3 rel-L2 {errs['bf16x3']:.3e}")
+    assert errs["bf16x3"] <= 1e-6
+    assert 1e-6 < errs["bf16x2"] <= 1e-4
+    assert errs["bf16x2"] > 10 * errs["bf16x3"]
+
+
+def tc_accumulation_probe(g):
+    """The tensor core's FP32 accumulation, measured: a b = 16, n = 3 plan with
+    W = all ones (exact in BF16, so the split leaves W1 = W2 = 0) applied to a
+    vector whose only nonzero fibre is x[k, 0, 0], k = 0..15, with values exact
+    in BF16 (x1 = x2 = 0).  Every output y[j, *, *] is then the tensor core's
+    FP32 sum of the 16 products of one MMA, passed unchanged through the other
+    two modes.  Returns the classification of three cases."""
+    W = np.ones((16, 16), dtype=np.float32)
+    cases = {
+        # 2^24 + 1.5: round to nearest gives 2^24 + 2, truncation 2^24
+        "rounding": ([2.0 ** 24, 1.5] + [0.0] * 14, {2.0 ** 24 + 2: "round-to-nearest", 2.0 ** 24: "truncation"}),
+        # 1 then fifteen 2^-25: FP32 additions in order lose them all (1.0); a
+        # wider sum (or the small terms combined first) gives 1 + 15 * 2^-25 rounded
+        "small_terms_after_large": ([1.0] + [2.0 ** -25] * 15,
+                                    {1.0: "each product rounded into an FP32 running sum",
+                                     float(np.float32(1 + 4 * 2.0 ** -23)): "sum wider than FP32, rounded once (nearest)",
+                                     float(np.float32(1 + 3 * 2.0 ** -23)): "sum wider than FP32, rounded once (truncated)"}),
+        "small_terms_before_large": ([2.0 ** -25] * 15 + [1.0],
+                                     {1.0: "small terms rounded away",
+                                      float(np.float32(1 + 4 * 2.0 ** -23)): "small terms kept (exact partial sums), rounded to nearest",
+                                      float(np.float32(1 + 3 * 2.0 ** -23)): "small terms kept (exact partial sums), truncated"}),
+    }
+    out = {}
+    plan = g.Plan(W, 3, "f32", 1)
+    plan.set_precision(g.PREC_BF16X3)
+    for name, (vals, meaning) in cases.items():
+        x = np.zeros((16, 16, 16), dtype=np.float32)   # [k2][k1][k0]: natural index k0 + 16 k1 + 256 k2
+        x[0, 0, :] = np.asarray(vals, dtype=np.float32)
+        y = plan.forward(torch.from_numpy(x.reshape(1, -1)).cuda()).cpu().numpy().reshape(16, 16, 16)
+        got = set(float(v) for v in np.unique(y))
+        assert len(got) == 1, (name, got)           # every output is the same 16-term sum
+        v = got.pop()
+        out[name] = {"value": v, "reading": meaning.get(v, "none of the modelled readings")}
+    return out
+
+
+def test_tensor_core_fp32_accumulation_is_measured(g):
+    res = tc_accumulation_probe(g)
+    print("tensor-core FP32 accumulation:", res)
+    for name, r in res.items():
+        assert r["reading"] != "none of the modelled readings", (name, r)
