@@ -539,7 +539,7 @@ def extra_b16(g, dev, hbm, reps=10, batch=64):
     res = {}
     outs = {}
     for name, prec in (("fp32_cuda_core", g.PREC_FP32), ("bf16x3_tcgen05", g.PREC_BF16X3),
-                       ("bf16x2_tcgen05", g.PREC_BF16X2)):
+                       ("bf16x2_tcgen05", g.PREC_BF16X2), ("tf32x3_tcgen05", g.PREC_TF32X3)):
         p2 = g.Plan(W2, 6, "f32", batch)
         p2.set_precision(prec)
         y2d = torch.empty_like(x2d)

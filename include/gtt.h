@@ -74,11 +74,14 @@ typedef enum {
                             splits (x0 W0 + x0 W1 + x1 W0), about 2^-16 relative
                             per mode; the cheaper reading of split BF16, kept to
                             compare with BF16X3                                     */
-    GTT_PREC_TF32X3 = 3  /* complex64, b = 4, opt-in: pairs of digits as one base-16
-                            digit with W (x) W, tcgen05 TF32 products of 2-piece
-                            splits (three products), FP32 accumulate; the digits
-                            left over in each pass on CUDA cores in FP32; two HBM
-                            round trips for n = 13 (slower than FP32 on GB300)      */
+    GTT_PREC_TF32X3 = 3  /* opt-in, tcgen05 TF32 products of 2-piece splits (three
+                            products; x rounded to nearest TF32, A operand in tensor
+                            memory), FP32 accumulate.  b = 16 FP32: each mode on the
+                            tensor cores, about 2^-21 relative per mode.  complex64,
+                            b = 4: pairs of digits as one base-16 digit with W (x) W,
+                            the digits left over in each pass on CUDA cores in FP32,
+                            two HBM round trips for n = 13 (slower than FP32 on
+                            GB300)                                                   */
 } gtt_precision_t;
 
 /*
@@ -131,7 +134,7 @@ gtt_status_t gtt_plan_set_w(gtt_plan_t plan, const void *W);
 
 /* Select the arithmetic of the mode contractions (gtt_precision_t).
  * GTT_PREC_BF16X3 and GTT_PREC_BF16X2 require b = 16, dtype F32 and n >= 3; GTT_PREC_TF32X3
- * requires b = 4, dtype C64 and n = 7 + 6k (k >= 0): a 7-digit pass and k
+ * requires the same, or b = 4, dtype C64 and n = 7 + 6k (k >= 0): a 7-digit pass and k
  * 6-digit passes, each one HBM round trip (thread-block clusters of four CTAs
  * exchange one digit through distributed shared memory); otherwise
  * GTT_ERR_UNSUPPORTED.  A tensor-core path has one fixed schedule:

@@ -341,7 +341,9 @@ static void set_w_bytes(gtt_plan_s *P, const void *W) {
 extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
     if (!P || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or W");
     set_w_bytes(P, W);
-    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2) return tc_upload_w(P);
+    if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2 ||
+        (P->precision == GTT_PREC_TF32X3 && P->b == 16))
+        return tc_upload_w(P);
     if (P->precision == GTT_PREC_TF32X3) return tcx_upload_w(P);
     return GTT_OK;
 }
@@ -395,7 +397,7 @@ static gtt_status_t use_tensor_cores(gtt_plan_s *P, int np = 3) {
     st = tc_upload_w(P);
     if (st != GTT_OK) return st;
     P->passes = passes;
-    P->precision = np == 3 ? GTT_PREC_BF16X3 : GTT_PREC_BF16X2;
+    P->precision = np == 3 ? GTT_PREC_BF16X3 : np == 2 ? GTT_PREC_BF16X2 : GTT_PREC_TF32X3;
     return GTT_OK;
 }
 
@@ -641,7 +643,7 @@ extern "C" gtt_status_t gtt_plan_set_precision(gtt_plan_t P, int precision) {
     if (precision == GTT_PREC_FP32) return use_cuda_core(P);
     if (precision == GTT_PREC_BF16X3) return use_tensor_cores(P, 3);
     if (precision == GTT_PREC_BF16X2) return use_tensor_cores(P, 2);
-    if (precision == GTT_PREC_TF32X3) return use_complex_tensor_cores(P);
+    if (precision == GTT_PREC_TF32X3) return P->b == 16 ? use_tensor_cores(P, 0) : use_complex_tensor_cores(P);
     if (precision == GTT_PREC_AUTO) {
         if (tc_eligible(P) && use_tensor_cores(P) == GTT_OK) return GTT_OK;
         return use_cuda_core(P);

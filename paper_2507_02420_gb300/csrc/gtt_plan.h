@@ -36,6 +36,7 @@ struct TmaPass {
 struct TcPass {
     bool on = false;
     int g = 0;
+    int np = 3;  // pieces: 3 (BF16X3), 2 (BF16X2) or 0 (TF32X3)
     const void *kern = nullptr;
     int grid = 0, block = 0, ctas_per_sm = 0;
     size_t smem = 0;
@@ -156,7 +157,7 @@ gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits,
                                     std::vector<PassPlan> *out);
 // b = 16 tensor-core passes (gtt_tc16.cu)
 gtt_status_t tc_upload_w(gtt_plan_s *P);
-gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out);  // np = 3 (BF16X3) or 2 (BF16X2)
+gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out);  // np = 3 (BF16X3), 2 (BF16X2), 0 (TF32X3)
 gtt_status_t tc_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s,
                     long long tile_begin, long long tile_end);
 // complex64 b = 4 tensor-core passes (gtt_tcx.cu)

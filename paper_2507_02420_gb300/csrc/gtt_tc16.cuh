@@ -20,6 +20,12 @@
 // x0 W1, x1 W0 into C0 and C1, y = C1 + C0) leaves the x residual and x1 W1,
 // about 2^-16 relative per mode: the cheaper, less accurate reading of "bf16x3"
 // (BF16X2 in the C ABI), kept for the precision comparison.
+// The TF32 variant (NP = 0, TF32X3 in the C ABI): x = x0 + x1 with x0 = x
+// rounded to TF32 (to nearest on the bit pattern) and x1 = x - x0, W = W0 + W1
+// (TF32 pieces rounded on the host); the two A pieces go to tensor memory
+// (tcgen05.st; the MMA reads A from there), and x0 [W0|W1] (N = 32) plus
+// x1 W0 (N = 16) accumulate C0 and C1, y = C1 + C0.  About 2^-21 relative per
+// mode: fewer instructions per element than the BF16 splits, within 1e-6.
 //
 // Operands (shared memory, K-major, no swizzle): core matrices of 8 rows x 16
 // bytes, the two K-halves 128 bytes apart (leading byte offset) and 8-row
@@ -38,9 +44,14 @@ constexpr int kTcBufs = 3;                   // tile ring: the tile in work and 
 constexpr uint32_t kTcTileBytes = kTcTile * 4;
 constexpr uint32_t kTcTmemCols = 128;        // two M blocks x 64 columns (48 used)
 constexpr uint32_t kTcPieceBytes = 8192;     // one BF16 piece of the A operand: 256 rows x 16
-constexpr uint32_t kTcWBytes = 1536;         // B operand: 48 rows x 16 BF16
-// ring, A pieces, B operand, mbarrier + TMEM slot, and slack for 128-byte alignment: 3 CTAs/SM
-constexpr size_t kTcSmemPerCta = kTcBufs * kTcTileBytes + 3 * kTcPieceBytes + kTcWBytes + 16 + 128;
+constexpr uint32_t kTcWBytes = 2048;         // B operand: 48 rows x 16 BF16 (1536 bytes), or 32 rows x 16 TF32
+constexpr uint32_t kTcWBf16Bytes = 1536, kTcWTf32Bytes = 2048;
+// ring, A pieces (BF16 variants; the TF32 variant keeps A in tensor memory), B
+// operand, mbarrier + TMEM slot, and slack for 128-byte alignment
+__host__ __device__ constexpr size_t tc_smem_per_cta(int np) {
+    return kTcBufs * kTcTileBytes + (np == 0 ? 0 : 3 * kTcPieceBytes) + kTcWBytes + 16 + 128;
+}
+constexpr size_t kTcSmemPerCta = tc_smem_per_cta(3);
 
 struct TcParams {
     PassParams p;              // tile geometry: tile_elems = 4096, r = 16^(3-g)
@@ -68,6 +79,34 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
                      d_tmem),
                  "l"(a), "l"(b), "r"(idesc), "r"(acc)
                  : "memory");
+}
+
+// K-major TF32 B operand (32 rows x 16): core matrices of 8 rows x 16 bytes,
+// K-neighbours 128 bytes apart, 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t umma_sdesc_tf32(uint32_t saddr_bytes) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr_bytes & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+// D (tensor memory) += A (tensor memory) * B (shared memory)^T, TF32
+__device__ __forceinline__ void umma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+                     d_tmem),
+                 "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -126,6 +165,7 @@ __device__ __forceinline__ void tc_fibre(uint32_t m, uint32_t (&off)[16]) {
 }
 
 struct TcCtx {
+    uint32_t colA0 = 0;    // TF32 variant: A0 column offset within the thread's M block (A1 at +16)
     uint32_t m;            // fibre of this thread (= row of the A operand)
     uint32_t tmem;         // base of the TMEM allocation (lane 0, first column)
     uint32_t tmem_row;     // this thread's accumulator row: its lane, its M block's columns
@@ -153,11 +193,23 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = S[off[k]];
     }
-    // split into three BF16 pieces, written K-major (two 16-byte rows per piece);
-    // residuals x - piece are exact, formed as one packed FMA per pair
+    // split into pieces: TF32 (NP = 0) into tensor memory, BF16 K-major into
+    // shared memory; residuals x - piece are exact
     const float2 neg1 = make_float2(-1.f, -1.f);
+    if constexpr (NP == 0) {
+        uint32_t t0[16], t1[16];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t u = (__float_as_uint(v[k]) + 0x1000u) & 0xFFFFE000u;  // to nearest TF32
+            t0[k] = u;
+            t1[k] = __float_as_uint(v[k] - __uint_as_float(u));
+        }
+        tmem_st16(c.tmem_row + c.colA0, t0);
+        tmem_st16(c.tmem_row + c.colA0 + 16u, t1);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+#pragma unroll
+    for (int h = 0; h < (NP == 0 ? 0 : 2); ++h) {
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -178,7 +230,7 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
         *reinterpret_cast<uint4 *>(c.A + kTcPieceBytes + ko) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
         if (NP == 3) *reinterpret_cast<uint4 *>(c.A + 2 * kTcPieceBytes + ko) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
     }
-    fence_proxy_async();  // generic-proxy writes of A, visible to the tensor core
+    if (NP != 0) fence_proxy_async();  // generic-proxy writes of A, visible to the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -187,7 +239,16 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
         for (uint32_t b2 = 0; b2 < 2; ++b2) {
             const uint32_t dcol = c.tmem + b2 * 64u;
             const uint32_t aoff = c.a_smem + b2 * 4096u;  // rows 128 b2 .. (16 groups x 256 B)
-            if (NP == 3) {
+            if (NP == 0) {
+                // M block b2: A0 in columns 64 b2 .. +15, A1 in +16 .. +31, D in +32 .. +63
+                const uint32_t a0 = c.tmem + b2 * 64u, d = a0 + 32u;
+#pragma unroll
+                for (uint32_t s = 0; s < 2; ++s)  // x0 [W0|W1]^T into D[0:32]
+                    umma_tf32_ts(d, a0 + 8u * s, c.descB + ((256u * s) >> 4), umma_idesc_tf32(32), s > 0);
+#pragma unroll
+                for (uint32_t s = 0; s < 2; ++s)  // + x1 W0^T into D[0:16]
+                    umma_tf32_ts(d, a0 + 16u + 8u * s, c.descB + ((256u * s) >> 4), umma_idesc_tf32(16), 1u);
+            } else if (NP == 3) {
                 umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(48), 0u);
                 umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(32), 1u);
                 umma_bf16(dcol + 32u, umma_sdesc(aoff + 2 * kTcPieceBytes), c.descB, umma_idesc(16), 1u);
@@ -205,9 +266,10 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float c0[16], c1[16], c2[16];
-    tmem_ld16(c.tmem_row, c0);
-    tmem_ld16(c.tmem_row + 16u, c1);
-    if (NP == 3) tmem_ld16(c.tmem_row + 32u, c2);
+    const uint32_t drow = c.tmem_row + (NP == 0 ? 32u : 0u);  // this thread's accumulator row
+    tmem_ld16(drow, c0);
+    tmem_ld16(drow + 16u, c1);
+    if (NP == 3) tmem_ld16(drow + 32u, c2);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     float y[16];
 #pragma unroll
@@ -249,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
     unsigned char *base = smem_raw + ((128u - (raw & 127u)) & 127u);
     float *ring = reinterpret_cast<float *>(base);
     unsigned char *A = base + kTcBufs * kTcTileBytes;
-    unsigned char *Bw = A + 3 * kTcPieceBytes;
+    unsigned char *Bw = A + (NP == 0 ? 0 : 3 * kTcPieceBytes);
     uint64_t *bar = reinterpret_cast<uint64_t *>(Bw + kTcWBytes);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(Bw + kTcWBytes + 8);
     const PassParams &p = tp.p;
@@ -276,7 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
     c.tmem_row = tmem + (((warp & 3u) * 32u) << 16) + (warp >> 2) * 64u;
     c.a_smem = smem_addr(A);
     c.bar = smem_addr(bar);
-    c.descB = umma_sdesc(smem_addr(Bw));
+    c.descB = NP == 0 ? umma_sdesc_tf32(smem_addr(Bw)) : umma_sdesc(smem_addr(Bw));
     c.A = A;
     uint32_t phase = 0;
     bool failed = false, bad = false;

@@ -204,3 +204,30 @@ def test_tensor_core_fp32_accumulation_is_measured(g):
     print("tensor-core FP32 accumulation:", res)
     for name, r in res.items():
         assert r["reading"] != "none of the modelled readings", (name, r)
+
+
+@pytest.mark.parametrize("n,batch", [(3, 4), (4, 3), (5, 2), (6, 1)])
+def test_tf32x3_b16_matches_oracle(g, n, batch):
+    """b = 16 FP32 on the TF32 two-piece path (A operand in tensor memory):
+    forward and adjoint against the FP64 oracle within the 1e-6 gate."""
+    rng = np.random.default_rng(9600 + n)
+    W = gi.haar_orthogonal(16, rng).astype(np.float32)
+    x = gi.normal_x((batch, 16 ** n), rng, np.float32)
+    plan = g.Plan(W, n, "f32", batch)
+    plan.set_precision(g.PREC_TF32X3)
+    d = plan.describe()
+    assert d["precision"] == "tf32x3" and all("tf32x3" in p["kernel"] for p in d["passes"]), d
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    z = plan.inverse(y)
+    torch.cuda.synchronize()
+    plan.check()
+    ref = oracle.modes(W.astype(np.float64), x.astype(np.float64))
+    e, e_rt = rel(y.cpu().numpy(), ref), rel(z.cpu().numpy(), x.astype(np.float64))
+    print(f"tf32x3 b=16 n={n}: forward rel-L2 {e:.3e}, inverse(forward) {e_rt:.3e}")
+    assert e <= 1e-6 and e_rt <= 2e-6
+    # a non-orthogonal W: the adjoint transform against the oracle's
+    W2 = (rng.standard_normal((16, 16)) * 0.3).astype(np.float32)
+    plan.set_w(W2)
+    zz = plan.inverse(xd).cpu().numpy()
+    assert rel(zz, oracle.adjoint(W2.astype(np.float64), x.astype(np.float64))) <= 1e-6
