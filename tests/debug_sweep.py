@@ -70,7 +70,7 @@ def main():
     pi = g.Plan(np.array([[1, 1], [1, -1]], dtype=np.int32), 6, "i32", 3)
     pi.forward(torch.from_numpy(xi).cuda())
     pi.check()
-    for prec in (g.PREC_BF16X3, g.PREC_BF16X2):
+    for prec in (g.PREC_BF16X3, g.PREC_BF16X2, g.PREC_TF32X3):
         for n in (3, 4, 5):
             W, x = make(16, n, 3, "f32", rng)
             plan = g.Plan(W, n, "f32", 3)
