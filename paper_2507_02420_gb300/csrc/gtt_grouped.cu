@@ -99,33 +99,7 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
         // an inverse); the scratch plan supplies the schedule only -- the
         // grouped kernel stages its tiles itself
         gtt_plan_set_w(P, R.W);
-        std::vector<unsigned char> Wb = R.inverse ? P->Wa : P->Wf;
-        if (R.dtype == GTT_C64) {  // GroupWc64: (wa, wb) of each entry side by side
-            const size_t bb = (size_t)R.b * R.b;
-            std::vector<float> wab(4 * bb);
-            const float *wa = reinterpret_cast<const float *>(Wb.data() + 8 * bb);
-            const float *wb = reinterpret_cast<const float *>(Wb.data() + 16 * bb);
-            for (size_t e = 0; e < bb; ++e) {
-                wab[4 * e] = wa[2 * e];
-                wab[4 * e + 1] = wa[2 * e + 1];
-                wab[4 * e + 2] = wb[2 * e];
-                wab[4 * e + 3] = wb[2 * e + 1];
-            }
-            Wb.assign(reinterpret_cast<const unsigned char *>(wab.data()),
-                      reinterpret_cast<const unsigned char *>(wab.data()) + wab.size() * sizeof(float));
-        } else if (R.b % 2 == 1) {  // GroupWf32odd: row pairs, then the last row
-            const int b = R.b;
-            std::vector<float> wg;
-            const float *w = reinterpret_cast<const float *>(Wb.data());
-            for (int ip = 0; ip < b / 2; ++ip)
-                for (int j = 0; j < b; ++j) {
-                    wg.push_back(w[(2 * ip) * b + j]);
-                    wg.push_back(w[(2 * ip + 1) * b + j]);
-                }
-            for (int j = 0; j < b; ++j) wg.push_back(w[(b - 1) * b + j]);
-            Wb.assign(reinterpret_cast<const unsigned char *>(wg.data()),
-                      reinterpret_cast<const unsigned char *>(wg.data()) + wg.size() * sizeof(float));
-        }
+        const std::vector<unsigned char> &Wb = R.inverse ? P->Wa : P->Wf;
         const size_t off = (wblob.size() + 15) / 16 * 16;
         wblob.resize(off + Wb.size());
         memcpy(wblob.data() + off, Wb.data(), Wb.size());

@@ -17,13 +17,11 @@
 // a wait only ever points to earlier items, so no cycle forms.  Each wait is
 // still bounded (kGroupSpinLimit polls) and an expiry raises the error flag.
 //
-// W of every request lives in a device blob (the kernels' parameter layout,
-// except complex64: GroupWc64); an item copies its W into shared memory unless
-// the previous item of the CTA had the same W.  Tile data is read with L2-coherent loads (ld.global.cg, 16
+// W of every request lives in a device blob (the kernels' parameter layout);
+// an item copies its W into shared memory unless the previous item of the CTA
+// had the same W.  Tile data is read with L2-coherent loads (ld.global.cg, 16
 // bytes wide where the tile rows allow): an earlier pass on another SM wrote it.
 #pragma once
-#include <type_traits>
-
 #include "gtt_internal.h"
 
 namespace gtt {
@@ -99,119 +97,10 @@ __device__ __forceinline__ void group_prefetch(const unsigned char *in, int es, 
     }
 }
 
-// complex64 W of a grouped request in shared memory: the packed pairs
-// wa = (re, re) and wb = (-im, im) of each entry side by side, so that one
-// 16-byte shared load serves a complex MAC (WMat keeps them in two arrays,
-// which is free in the constant bank but costs two shared loads here)
-template <int B> struct GroupWc64 {
-    float4 wab[B * B];
-};
-
-// apply_digit's complex64 arithmetic with W in the GroupWc64 layout: the same
-// operations in the same order, so results equal the single-transform kernels'
-template <int B, int D, int K>
-__device__ __forceinline__ void group_digit_c64(c64 (&v)[cpow(B, D)], const GroupWc64<B> &W) {
-    constexpr int S = cpow(B, K);
-#pragma unroll
-    for (int o = 0; o < cpow(B, D) / B; ++o) {
-        const int base = (o / S) * S * B + (o % S);
-        float2 in[B], sw[B], acc[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            in[j] = make_float2(v[base + j * S].re, v[base + j * S].im);
-            sw[j] = make_float2(v[base + j * S].im, v[base + j * S].re);
-        }
-        // each output sums j = 0..B-1 in order, wa before wb (as apply_digit)
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-#pragma unroll
-            for (int i = 0; i < B; ++i) {
-                const float4 q = W.wab[i * B + j];
-                acc[i] = __ffma2_rn(make_float2(q.x, q.y), in[j], j == 0 ? make_float2(0.f, 0.f) : acc[i]);
-                acc[i] = __ffma2_rn(make_float2(q.z, q.w), sw[j], acc[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < B; ++i) v[base + i * S] = c64{acc[i].x, acc[i].y};
-    }
-}
-
-template <int B, int D, int K = 0>
-__device__ __forceinline__ void group_window_c64(c64 (&v)[cpow(B, D)], int mask, const GroupWc64<B> &W) {
-    if constexpr (K < D) {
-        if (mask & (1 << K)) group_digit_c64<B, D, K>(v, W);
-        group_window_c64<B, D, K + 1>(v, mask, W);
-    }
-}
-
-// FP32 W of odd size in shared memory: row pairs wp[ip*B + j] = (W[2ip][j],
-// W[2ip+1][j]) for packed FMAs, and the last row wl; two rows per 8-byte load
-template <int B> struct GroupWf32odd {
-    float2 wp[(B / 2) * B];
-    float wl[B];
-};
-
-// apply_digit's FP32 arithmetic with W in the GroupWf32odd layout: each
-// output is W[i][0] x[0] followed by the FMAs over j = 1..B-1 in order
-template <int B, int D, int K>
-__device__ __forceinline__ void group_digit_f32odd(float (&v)[cpow(B, D)], const GroupWf32odd<B> &W) {
-    constexpr int S = cpow(B, K);
-#pragma unroll
-    for (int o = 0; o < cpow(B, D) / B; ++o) {
-        const int base = (o / S) * S * B + (o % S);
-        float in[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) in[j] = v[base + j * S];
-        float2 acc[B / 2];
-        float last = W.wl[0] * in[0];
-#pragma unroll
-        for (int ip = 0; ip < B / 2; ++ip) {
-            const float2 w = W.wp[ip * B];
-            acc[ip] = make_float2(w.x * in[0], w.y * in[0]);
-        }
-#pragma unroll
-        for (int j = 1; j < B; ++j) {
-#pragma unroll
-            for (int ip = 0; ip < B / 2; ++ip) acc[ip] = __ffma2_rn(W.wp[ip * B + j], make_float2(in[j], in[j]), acc[ip]);
-            last = fmaf(W.wl[j], in[j], last);
-        }
-#pragma unroll
-        for (int ip = 0; ip < B / 2; ++ip) {
-            v[base + 2 * ip * S] = acc[ip].x;
-            v[base + (2 * ip + 1) * S] = acc[ip].y;
-        }
-        v[base + (B - 1) * S] = last;
-    }
-}
-
-template <int B, int D, int K = 0>
-__device__ __forceinline__ void group_window_f32odd(float (&v)[cpow(B, D)], int mask, const GroupWf32odd<B> &W) {
-    if constexpr (K < D) {
-        if (mask & (1 << K)) group_digit_f32odd<B, D, K>(v, W);
-        group_window_f32odd<B, D, K + 1>(v, mask, W);
-    }
-}
-
-template <typename T, int B> struct GroupW { using type = WMat<T, B>; };
-template <int B> struct GroupW<c64, B> { using type = GroupWc64<B>; };
-template <> struct GroupW<float, 3> { using type = GroupWf32odd<3>; };
-template <> struct GroupW<float, 5> { using type = GroupWf32odd<5>; };
-template <> struct GroupW<float, 7> { using type = GroupWf32odd<7>; };
-
-template <typename T, int B, int D>
-__device__ __forceinline__ void group_window(T (&v)[cpow(B, D)], int mask, const typename GroupW<T, B>::type &W) {
-    if constexpr (std::is_same<T, c64>::value)
-        group_window_c64<B, D>(v, mask, W);
-    else if constexpr (std::is_same<T, float>::value && B % 2 == 1)
-        group_window_f32odd<B, D>(v, mask, W);
-    else
-        apply_window<T, B, D>(v, mask, W);
-}
-
 // One tile of one pass (shared-memory staging as in gtt_pass_kernel).
 template <typename T, int B, int D>
 __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p, long long t, T *__restrict__ s,
-                                        const typename GroupW<T, B>::type &W) {
+                                        const WMat<T, B> &W) {
     constexpr int RB = cpow(B, D);
     constexpr int CE = Vec16<T>::n;
     const uint32_t tid = threadIdx.x, nth = blockDim.x;
@@ -275,7 +164,7 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
             T v[RB];
 #pragma unroll
             for (int q = 0; q < RB; ++q) v[q] = s[spos<RB>(e0 + q * strideA)];
-            group_window<T, B, D>(v, mask, W);
+            apply_window<T, B, D>(v, mask, W);
 #pragma unroll
             for (int q = 0; q < RB; ++q) s[spos<RB>(e0 + q * strideA)] = v[q];
         }
@@ -318,7 +207,7 @@ __device__ __forceinline__ void group_dispatch_d(const GroupReq &rq, const Group
     constexpr int DM = dmax_bytes((int)sizeof(T), B);
     const T *in = reinterpret_cast<const T *>(first ? rq.x : (const void *)rq.y);
     T *out = reinterpret_cast<T *>(rq.y);
-    const typename GroupW<T, B>::type &W = *reinterpret_cast<const typename GroupW<T, B>::type *>(smem);
+    const WMat<T, B> &W = *reinterpret_cast<const WMat<T, B> *>(smem);
     T *s = reinterpret_cast<T *>(smem + w_smem_bytes);
     if (gp.D == DM)
         group_tile<T, B, DM>(in, out, gp.p, t, s, W);

@@ -94,15 +94,10 @@ static const void *tc_kernel(int g, int np) {
                   : g == 2 ? (const void *)&gtt_tc16_pass_kernel<2, 3> : (const void *)&gtt_tc16_pass_kernel<1, 3>;
 }
 
-static const void *tc_r4_kernel(int np) {
-    return np == 0 ? (const void *)&gtt_tc16_r4_kernel<0>
-                   : np == 2 ? (const void *)&gtt_tc16_r4_kernel<2> : (const void *)&gtt_tc16_r4_kernel<3>;
-}
-
 // CTAs of a tensor-core pass kernel per SM, from the register and shared-memory
 // budgets (the occupancy query under-reports kernels that allocate tensor
 // memory), capped by the 4 x 128 TMEM columns of an SM; 0 on failure
-static int tc_residency(gtt_plan_s *P, const void *k, size_t smem) {
+static int tc_residency(gtt_plan_s *P, const void *k, int np) {
     if (allow_max_smem(k, P->smem_optin) != cudaSuccess ||
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return 0;
@@ -112,13 +107,12 @@ static int tc_residency(gtt_plan_s *P, const void *k, size_t smem) {
     cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, P->device);
     cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device);
     const int by_regs = regs_per_sm / std::max(1, fa.numRegs * kTcThreads);
-    const int by_smem = smem_per_sm / (int)(smem + 1024);
+    const int by_smem = smem_per_sm / (int)(tc_smem_per_cta(np) + 1024);
     return std::min(std::min(by_regs, by_smem), 4);
 }
 
-// Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (3, r=4)
-// passes while three digits are left, then (2, r=16) and a final (1, r=256)
-// pass for what remains.
+// Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (2, r=16)
+// passes, and a final (1, r=256) pass when one digit is left.
 gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out) {
     if (P->b != 16 || P->dtype != GTT_F32 || P->n < 3)
         return set_error(GTT_ERR_UNSUPPORTED, "the b = 16 tensor-core paths need b = 16, FP32 and n >= 3");
@@ -126,12 +120,10 @@ gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out)
     int m0 = 0;
     while (m0 < P->n) {
         const int left = P->n - m0;
-        const int g = m0 == 0 ? 3 : (left >= 3 ? 3 : left >= 2 ? 2 : 1);
-        const bool r4 = m0 > 0 && g == 3;
-        const long long r = m0 == 0 ? 1 : r4 ? 4 : (g == 2 ? 16 : 256);
-        const void *k = r4 ? tc_r4_kernel(np) : tc_kernel(g, np);
-        const size_t smem = r4 ? tc_r4_smem_per_cta(np) : tc_smem_per_cta(np);
-        const int per_sm = tc_residency(P, k, smem);
+        const int g = m0 == 0 ? 3 : (left >= 2 ? 2 : 1);
+        const long long r = m0 == 0 ? 1 : (g == 2 ? 16 : 256);
+        const void *k = tc_kernel(g, np);
+        const int per_sm = tc_residency(P, k, np);
         if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, 1, &pp);
@@ -142,10 +134,10 @@ gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out)
         pp.tc.grid = (int)std::min<long long>((long long)per_sm * P->num_sms, pp.params.tiles);
         pp.tc.ctas_per_sm = per_sm;
         pp.tc.block = kTcThreads;
-        pp.tc.smem = smem;
+        pp.tc.smem = tc_smem_per_cta(np);
         pp.tc.np = np;
-        pp.tc.name = std::string(r4 ? "gtt_tc16_r4_kernel<" : "gtt_tc16_pass_kernel<") +
-                     (np == 3 ? "bf16x3" : np == 2 ? "bf16x2" : "tf32x3") + ",g=" + std::to_string(g) + ">";
+        pp.tc.name = std::string("gtt_tc16_pass_kernel<") + (np == 3 ? "bf16x3" : np == 2 ? "bf16x2" : "tf32x3") + ",g=" +
+                     std::to_string(g) + ">";
         passes.push_back(pp);
         m0 += g;
     }

@@ -174,17 +174,16 @@ struct TcCtx {
     unsigned char *A;
 };
 
-// One mode step: read this thread's fibre at S[off[k]] (RD = 1: as four
-// 16-byte chunks starting at off[0], off[4], off[8], off[12]), split it into
-// pieces (the A operand), run the MMAs into TMEM, and write y back: WR = 0 to
-// S[off[n]], WR = 1 as four 16-byte chunks, WR = 2 to global memory at
-// o[n * stride_n].  Returns false in a thread whose wait for the MMA
-// completion timed out.
-template <int NP, int RD, int WR>
-__device__ __forceinline__ bool tc_core(const TcCtx &c, float *S, const uint32_t (&off)[16], uint32_t &phase, float *o,
-                                        long long stride_n) {
+// One mode of the tile in S: read fibre m, split it into three BF16 pieces
+// (the A operand), run the BF16x3 MMAs into TMEM, and write y_m back to S
+// (D < 2) or, for the last mode, straight to global memory at o[n * stride_n].
+// Returns false in a thread whose wait for the MMA completion timed out.
+template <int D, int NP>
+__device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phase, float *o, long long stride_n) {
+    uint32_t off[16];
+    tc_fibre<D>(c.m, off);
     float v[16];
-    if (RD == 1) {
+    if (D == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const float4 t = *reinterpret_cast<const float4 *>(S + off[4 * q]);
@@ -280,30 +279,20 @@ __device__ __forceinline__ bool tc_core(const TcCtx &c, float *S, const uint32_t
                                  : __fadd2_rn(make_float2(c1[n], c1[n + 1]), make_float2(c0[n], c0[n + 1]));
         y[n] = s.x, y[n + 1] = s.y;
     }
-    if (WR == 1) {
+    if (D == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *reinterpret_cast<float4 *>(S + off[4 * q]) = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-    } else if (WR == 0) {
+    } else if (D == 1) {
 #pragma unroll
         for (int n = 0; n < 16; ++n) S[off[n]] = y[n];
     } else {
 #pragma unroll
         for (int n = 0; n < 16; ++n) o[n * stride_n] = y[n];
     }
-    // the next step issues MMAs into the same TMEM columns only after its own
+    // the next mode issues MMAs into the same TMEM columns only after its own
     // barrier, which every thread reaches after finishing these loads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    return ok;
-}
-
-// One mode of the 4096-element tile in S (fibre c.m along digit D), written
-// back to S (D < 2) or, for the last mode, straight to global memory.
-template <int D, int NP>
-__device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phase, float *o, long long stride_n) {
-    uint32_t off[16];
-    tc_fibre<D>(c.m, off);
-    const bool ok = tc_core<NP, D == 0 ? 1 : 0, D == 0 ? 1 : D == 1 ? 0 : 2>(c, S, off, phase, o, stride_n);
     // y_m in S, visible to the next mode.  Mode 0 -> mode 1 stays inside a
     // warp: element (h2, h1, h0) is written by thread h1 + 16 h2 and read by
     // thread h0 + 16 h2, both in warp h2 / 2.  Mode 1 -> mode 2 crosses warps.
@@ -409,168 +398,6 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
 #undef stride_n
 #endif
         slot = slot == 2 ? 0 : slot + 1;
-    }
-    if (!failed && __syncthreads_or(bad)) failed = true;  // the last tile's vote
-    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves
-    if (failed && tid == 0) atomicExch(tp.err, 1);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
-}
-
-// ------------------------------------------------------------ runs of four
-// Strided pass over three digits with runs of r = 4 consecutive low indices
-// (16 bytes): with the contiguous 3-digit first pass, n = 6 takes two HBM
-// round trips.  A tile is 4096 rows (the three digits, h0 fastest) of 4
-// floats; the 16-byte chunk of row (h2, h1, h0) sits at chunk position
-//   r4 position = 256 h2 + 16 h1 + (h0 ^ (h1 mod 8)).
-// A mode is four steps of 64 fibres each, every fibre with its four run
-// elements: thread t takes fibre 64 q + t / 4 of step q and run element t mod 4,
-// so a warp reads and writes 8 fibres x 4 run elements, and for every mode the
-// 8 fibres' chunks fall in 8 different 16-byte bank groups (conflict-free).
-// The tile is transformed in place and stored as 16-byte chunks after the last
-// mode.  One 64 KiB tile buffer per CTA: the next tile is prefetched into L2
-// while this one is transformed, and the other CTAs of the SM overlap the load.
-constexpr int kTcR4Tile = 4 * kTcTile;
-constexpr uint32_t kTcR4TileBytes = kTcR4Tile * 4;
-__host__ __device__ constexpr size_t tc_r4_smem_per_cta(int np) {
-    return kTcR4TileBytes + (np == 0 ? 0 : 3 * kTcPieceBytes) + kTcWBytes + 16 + 128;
-}
-
-__device__ __forceinline__ uint32_t r4_chunk_pos(uint32_t c) { return c ^ ((c >> 4) & 7u); }
-
-// Float offsets of the 16 elements of fibre f (0..255) of mode D, run element
-// rho: with lo = f mod 16, hi = f / 16 the fibre is (hi, lo, k) for D = 0,
-// (hi, k, lo) for D = 1 and (k, hi, lo) for D = 2.  The XOR with the row term
-// touches bits 2..4 only, so each offset is a per-thread base XOR 4 (k mod 8)
-// plus a constant.
-template <int D>
-__device__ __forceinline__ void r4_fibre(uint32_t f, uint32_t rho, uint32_t (&off)[16]) {
-    const uint32_t lo = f & 15u, hi = f >> 4;
-    if (D == 0) {
-        const uint32_t X = (hi * 1024u + lo * 64u + rho) | ((lo & 7u) << 2);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) off[k] = (X ^ ((uint32_t)(k & 7) << 2)) + 32u * (uint32_t)(k >> 3);
-    } else if (D == 1) {
-        const uint32_t X = hi * 1024u + lo * 4u + rho;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) off[k] = (X ^ ((uint32_t)(k & 7) << 2)) + 64u * (uint32_t)k;
-    } else {
-        const uint32_t X = hi * 64u + ((lo ^ (hi & 7u)) << 2) + rho;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) off[k] = X + 1024u * (uint32_t)k;
-    }
-}
-
-template <int NP>
-__global__ void __launch_bounds__(kTcThreads, 2) gtt_tc16_r4_kernel(const float *in, float *out, TcParams tp) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t raw = smem_addr(smem_raw);
-    unsigned char *base = smem_raw + ((128u - (raw & 127u)) & 127u);
-    float *S = reinterpret_cast<float *>(base);
-    unsigned char *A = base + kTcR4TileBytes;
-    unsigned char *Bw = A + (NP == 0 ? 0 : 3 * kTcPieceBytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bw + kTcWBytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(Bw + kTcWBytes + 8);
-    const PassParams &p = tp.p;
-    const uint32_t tid = threadIdx.x, warp = tid >> 5;
-
-    for (uint32_t i = tid; i < kTcWBytes / 16; i += kTcThreads)
-        reinterpret_cast<int4 *>(Bw)[i] = reinterpret_cast<const int4 *>(tp.wpieces)[i];
-    if (tid == 0) {
-        mbar_init(smem_addr(bar), 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(kTcTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    TcCtx c;
-    c.m = tid;  // row of the A operand; warp w reads TMEM lanes 32 (w mod 4) ..
-    c.tmem = tmem;
-    c.tmem_row = tmem + (((warp & 3u) * 32u) << 16) + (warp >> 2) * 64u;
-    c.a_smem = smem_addr(A);
-    c.bar = smem_addr(bar);
-    c.descB = NP == 0 ? umma_sdesc_tf32(smem_addr(Bw)) : umma_sdesc(smem_addr(Bw));
-    c.A = A;
-    uint32_t phase = 0;
-    bool failed = false, bad = false;
-    const uint32_t rho = tid & 3u, fq = tid >> 2;  // run element; fibre within a step
-
-    const long long LM = p.L * (long long)p.M;
-    const long long G0 = p.tile_begin + blockIdx.x, step = gridDim.x;
-    auto tile_base = [&](long long t) {
-        const long long hi = t / p.lo_blocks;
-        const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
-        return hi * LM + 4ll * lob;
-    };
-    // row cc of the tile: 4 floats at gb + cc * L
-    auto issue_load = [&](long long t) {
-        if (t < p.tiles) {
-            const long long gb = tile_base(t);
-#pragma unroll 4
-            for (int i = 0; i < kTcTile / kTcThreads; ++i) {
-                const uint32_t cc = tid + (uint32_t)i * kTcThreads;
-                const float *src = in + GTT_CHECKED(gb + (long long)cc * p.L, p.total - 3, tp.err);
-                const uint32_t dst = smem_addr(S + GTT_CHECKED(4u * r4_chunk_pos(cc), kTcR4Tile - 3, tp.err));
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    auto prefetch_l2 = [&](long long t) {
-        if (t < p.tiles) {
-            const long long gb = tile_base(t);
-#pragma unroll 4
-            for (int i = 0; i < kTcTile / kTcThreads; ++i) {
-                const uint32_t cc = tid + (uint32_t)i * kTcThreads;
-                const float *src = in + GTT_CHECKED(gb + (long long)cc * p.L, p.total - 3, tp.err);
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], 16;" ::"l"(src) : "memory");
-            }
-        }
-    };
-
-    issue_load(G0);
-    for (long long t = G0; t < p.tiles; t += step) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        if (__syncthreads_or(bad)) {  // uniform: an MMA wait of the last tile expired somewhere
-            failed = true;
-            break;
-        }
-        prefetch_l2(t + step);
-        uint32_t off[16];
-#pragma unroll 1
-        for (uint32_t q = 0; q < 4; ++q) {
-            r4_fibre<0>(64u * q + fq, rho, off);
-            bad |= !tc_core<NP, 0, 0>(c, S, off, phase, nullptr, 0);
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (uint32_t q = 0; q < 4; ++q) {
-            r4_fibre<1>(64u * q + fq, rho, off);
-            bad |= !tc_core<NP, 0, 0>(c, S, off, phase, nullptr, 0);
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (uint32_t q = 0; q < 4; ++q) {
-            r4_fibre<2>(64u * q + fq, rho, off);
-            bad |= !tc_core<NP, 0, 0>(c, S, off, phase, nullptr, 0);
-        }
-        __syncthreads();
-        const long long gb = tile_base(t);
-#pragma unroll 4
-        for (int i = 0; i < kTcTile / kTcThreads; ++i) {
-            const uint32_t cc = tid + (uint32_t)i * kTcThreads;
-            const float4 v = *reinterpret_cast<const float4 *>(S + 4u * r4_chunk_pos(cc));
-            *reinterpret_cast<float4 *>(out + GTT_CHECKED(gb + (long long)cc * p.L, p.total - 3, tp.err)) = v;
-        }
-        __syncthreads();  // the tile buffer is read before the next tile lands in it
-        issue_load(t + step);
     }
     if (!failed && __syncthreads_or(bad)) failed = true;  // the last tile's vote
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves

@@ -231,65 +231,3 @@ def test_tf32x3_b16_matches_oracle(g, n, batch):
     plan.set_w(W2)
     zz = plan.inverse(xd).cpu().numpy()
     assert rel(zz, oracle.adjoint(W2.astype(np.float64), x.astype(np.float64))) <= 1e-6
-
-
-TOL_PREC = {"bf16x3": 1e-6, "tf32x3": 1e-6, "bf16x2": 1e-4}
-
-
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "tf32x3"])
-def test_n6_runs_of_four_two_round_trips(g, prec):
-    """n = 6 in two HBM round trips: digits 0-2 on contiguous tiles, digits 3-5
-    on tiles of 4096 rows x 4 contiguous floats (the runs-of-four kernel).
-    Forward and adjoint against the FP64 oracle, batch 2, non-orthogonal W for
-    the adjoint."""
-    rng = np.random.default_rng(9700)
-    W = gi.haar_orthogonal(16, rng).astype(np.float32)
-    x = gi.normal_x((2, 16 ** 6), rng, np.float32)
-    plan = g.Plan(W, 6, "f32", 2)
-    plan.set_precision(getattr(g, "PREC_" + prec.upper()))
-    d = plan.describe()
-    assert len(d["passes"]) == 2 and "r4" in d["passes"][1]["kernel"] and prec in d["passes"][1]["kernel"], d
-    xd = torch.from_numpy(x).cuda()
-    y = plan.forward(xd)
-    z = xd.clone()
-    plan.forward(z, out=z)  # in place
-    torch.cuda.synchronize()
-    plan.check()
-    assert torch.equal(y, z)
-    ref = oracle.modes(W.astype(np.float64), x.astype(np.float64))
-    e = rel(y.cpu().numpy(), ref)
-    W2 = (rng.standard_normal((16, 16)) * 0.3).astype(np.float32)
-    plan.set_w(W2)
-    a = plan.inverse(xd)
-    e_adj = rel(a.cpu().numpy(), oracle.adjoint(W2.astype(np.float64), x.astype(np.float64)))
-    print(f"{prec} b=16 n=6, two round trips: forward rel-L2 {e:.3e}, adjoint {e_adj:.3e}")
-    assert e <= TOL_PREC[prec] and e_adj <= TOL_PREC[prec]
-
-
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
-def test_n7_runs_of_four_separable_closed_form(g, prec):
-    """n = 7 (268 M elements): passes of digits 0-2 (contiguous), 3-5 (runs of
-    four) and 6 (runs of 256).  A separable input u_0 (x) ... (x) u_6 maps to
-    W u_0 (x) ... (x) W u_6 (Def. 2.3), which gives the exact result at this size
-    without the oracle's full transform."""
-    rng = np.random.default_rng(9800)
-    W = gi.haar_orthogonal(16, rng).astype(np.float32)
-    us = [rng.standard_normal(16) for _ in range(7)]
-    x64 = us[0]
-    for u in us[1:]:
-        x64 = np.kron(x64, u)
-    x = x64.astype(np.float32)  # rounding the input costs about 2^-24 relative, far below the tolerance
-    y_ref = W.astype(np.float64) @ us[0]
-    for u in us[1:]:
-        y_ref = np.kron(y_ref, W.astype(np.float64) @ u)
-    del x64
-    plan = g.Plan(W, 7, "f32", 1)
-    plan.set_precision(getattr(g, "PREC_" + prec.upper()))
-    d = plan.describe()
-    assert [("r4" in p["kernel"]) for p in d["passes"]] == [False, True, False], d
-    y = plan.forward(torch.from_numpy(x).reshape(1, -1).cuda())
-    torch.cuda.synchronize()
-    plan.check()
-    e = rel(y.cpu().numpy().ravel(), y_ref)
-    print(f"{prec} b=16 n=7 separable: rel-L2 {e:.3e}")
-    assert e <= 1e-6
