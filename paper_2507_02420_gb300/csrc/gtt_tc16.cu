@@ -111,6 +111,16 @@ static int tc_residency(gtt_plan_s *P, const void *k, int np) {
     return std::min(std::min(by_regs, by_smem), 4);
 }
 
+// CTAs per SM at most, by variant (TF32X3; BF16X2 and BF16X3) and pass
+// (g = 1, 2, 3).  Measured on b16_n6_batch64: the g = 2 pass (64-byte runs at
+// a 16 KiB stride) slows down with more resident CTAs -- TF32X3 2112 / 1910 /
+// 1649 us at 4 / 3 / 2 CTAs per SM, BF16X3 1930 / 1627 / 1837 us -- while the
+// g = 3 pass is fastest at 4 (1591 against 1744 us at 3).
+static int tc_ctas_cap(int np, int g) {
+    static const int cap[2][3] = {{4, 2, 4}, {4, 3, 4}};
+    return cap[np == 0 ? 0 : 1][g - 1];
+}
+
 // Tensor-core schedule for b = 16, n >= 3: digits (3, r=1), then (2, r=16)
 // passes, and a final (1, r=256) pass when one digit is left.
 gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out) {
@@ -123,7 +133,7 @@ gtt_status_t make_tc_schedule(gtt_plan_s *P, int np, std::vector<PassPlan> *out)
         const int g = m0 == 0 ? 3 : (left >= 2 ? 2 : 1);
         const long long r = m0 == 0 ? 1 : (g == 2 ? 16 : 256);
         const void *k = tc_kernel(g, np);
-        const int per_sm = tc_residency(P, k, np);
+        const int per_sm = std::min(tc_residency(P, k, np), tc_ctas_cap(np, g));
         if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "tensor-core kernel cannot be resident");
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, 1, &pp);

@@ -10,12 +10,15 @@
 //
 // Precision: x = x0 + x1 + x2 and W = W0 + W1 + W2 with BF16 pieces
 // (round-to-nearest splits of the FP32 residuals).  The six products whose
-// order is at most 2^-16 relative are accumulated in three FP32 partial sums:
-//   C0 = x0 W0,  C1 = x0 W1 + x1 W0,  C2 = x0 W2 + x1 W1 + x2 W0,
-// computed by three MMAs against the concatenated B operands
-//   x0 . [W0|W1|W2] (N = 48), x1 . [W0|W1] (N = 32, into C1 C2), x2 . W0 (N = 16, into C2),
-// and y = (C2 + C1) + C0 on readback.  The dropped terms are below 2^-24
-// relative, so the result matches FP32 to within a few ulps.
+// order is at most 2^-16 relative are accumulated in two FP32 partial sums:
+//   C0 = x0 W0,  C12 = x0 W1 + x0 W2 + x1 W0 + x1 W1 + x2 W0,
+// and y = C12 + C0 on readback.  The x pieces go to tensor memory
+// (tcgen05.st, two BF16 per column; the MMA reads A from there) and B is
+// [W0|W1|W2] in shared memory: x0 [W0|W1] (N = 32) starts C0 and C12, and
+// four N = 16 MMAs add the other terms to C12.  The tensor core adds each
+// MMA's sum into its FP32 accumulator with truncation; C12 is about 2^-8 of
+// y, so that costs at most about 2^-29 of y per mode.  The dropped terms are
+// below 2^-24 relative, so the result matches FP32 to within a few ulps.
 // The two-piece variant (NP = 2: x = x0 + x1, W = W0 + W1, products x0 W0,
 // x0 W1, x1 W0 into C0 and C1, y = C1 + C0) leaves the x residual and x1 W1,
 // about 2^-16 relative per mode: the cheaper, less accurate reading of "bf16x3"
@@ -27,9 +30,10 @@
 // x1 W0 (N = 16) accumulate C0 and C1, y = C1 + C0.  About 2^-21 relative per
 // mode: fewer instructions per element than the BF16 splits, within 1e-6.
 //
-// Operands (shared memory, K-major, no swizzle): core matrices of 8 rows x 16
+// Shared-memory operands (K-major, no swizzle): core matrices of 8 rows x 16
 // bytes, the two K-halves 128 bytes apart (leading byte offset) and 8-row
-// groups 256 bytes apart (stride byte offset).  One elected thread issues the
+// groups 256 bytes apart (stride byte offset).  Only BF16X2 keeps its A pieces
+// there; the other variants hold A in tensor memory.  One elected thread issues the
 // MMAs; tcgen05.commit signals an mbarrier; every wait is bounded.
 #pragma once
 #include <cuda_bf16.h>
@@ -42,14 +46,14 @@ constexpr int kTcThreads = 256;
 constexpr int kTcTile = 4096;
 constexpr int kTcBufs = 3;                   // tile ring: the tile in work and two prefetched
 constexpr uint32_t kTcTileBytes = kTcTile * 4;
-constexpr uint32_t kTcTmemCols = 128;        // two M blocks x 64 columns (48 used)
+constexpr uint32_t kTcTmemCols = 128;        // two M blocks x 64 columns
 constexpr uint32_t kTcPieceBytes = 8192;     // one BF16 piece of the A operand: 256 rows x 16
 constexpr uint32_t kTcWBytes = 2048;         // B operand: 48 rows x 16 BF16 (1536 bytes), or 32 rows x 16 TF32
 constexpr uint32_t kTcWBf16Bytes = 1536, kTcWTf32Bytes = 2048;
-// ring, A pieces (BF16 variants; the TF32 variant keeps A in tensor memory), B
+// ring, A pieces (BF16X2; the others keep A in tensor memory), B
 // operand, mbarrier + TMEM slot, and slack for 128-byte alignment
 __host__ __device__ constexpr size_t tc_smem_per_cta(int np) {
-    return kTcBufs * kTcTileBytes + (np == 0 ? 0 : 3 * kTcPieceBytes) + kTcWBytes + 16 + 128;
+    return kTcBufs * kTcTileBytes + (np == 2 ? 2 * kTcPieceBytes : 0) + kTcWBytes + 16 + 128;
 }
 constexpr size_t kTcSmemPerCta = tc_smem_per_cta(3);
 
@@ -94,6 +98,13 @@ __device__ __forceinline__ uint64_t umma_sdesc_tf32(uint32_t saddr_bytes) {
 __host__ __device__ constexpr uint32_t umma_idesc_tf32(int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
+// D (tensor memory) += A (tensor memory) * B (shared memory)^T, BF16
+__device__ __forceinline__ void umma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+                     d_tmem),
+                 "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
 // D (tensor memory) += A (tensor memory) * B (shared memory)^T, TF32
 __device__ __forceinline__ void umma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
@@ -107,6 +118,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
         "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
         : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -208,6 +225,7 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
         tmem_st16(c.tmem_row + c.colA0 + 16u, t1);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
+    uint32_t pc[3][8];  // NP = 3: the pieces as packed BF16 pairs, k = 2j (low half) and 2j + 1
 #pragma unroll
     for (int h = 0; h < (NP == 0 ? 0 : 2); ++h) {
         uint32_t w0[4], w1[4], w2[4];
@@ -225,12 +243,26 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
             w1[q] = u1;
             w2[q] = *reinterpret_cast<const uint32_t *>(&p2);
         }
-        const uint32_t ko = kmaj_off(c.m, 8 * h);
-        *reinterpret_cast<uint4 *>(c.A + ko) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        *reinterpret_cast<uint4 *>(c.A + kTcPieceBytes + ko) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-        if (NP == 3) *reinterpret_cast<uint4 *>(c.A + 2 * kTcPieceBytes + ko) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        if (NP == 3) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                pc[0][4 * h + q] = w0[q];
+                pc[1][4 * h + q] = w1[q];
+                pc[2][4 * h + q] = w2[q];
+            }
+        } else {
+            const uint32_t ko = kmaj_off(c.m, 8 * h);
+            *reinterpret_cast<uint4 *>(c.A + ko) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+            *reinterpret_cast<uint4 *>(c.A + kTcPieceBytes + ko) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        }
     }
-    if (NP != 0) fence_proxy_async();  // generic-proxy writes of A, visible to the tensor core
+    if (NP == 3) {  // pieces p in columns 8p .. 8p + 7 of the thread's row (two BF16 per column)
+        tmem_st8(c.tmem_row, pc[0]);
+        tmem_st8(c.tmem_row + 8u, pc[1]);
+        tmem_st8(c.tmem_row + 16u, pc[2]);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    if (NP == 2) fence_proxy_async();  // generic-proxy writes of A, visible to the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -249,9 +281,15 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
                 for (uint32_t s = 0; s < 2; ++s)  // + x1 W0^T into D[0:16]
                     umma_tf32_ts(d, a0 + 16u + 8u * s, c.descB + ((256u * s) >> 4), umma_idesc_tf32(16), 1u);
             } else if (NP == 3) {
-                umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(48), 0u);
-                umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(32), 1u);
-                umma_bf16(dcol + 32u, umma_sdesc(aoff + 2 * kTcPieceBytes), c.descB, umma_idesc(16), 1u);
+                // M block b2: pieces x0, x1, x2 in columns 64 b2 + 0, 8, 16; C0 in
+                // +32 .. +47, C12 in +48 .. +63.  B rows 16p .. 16p + 15 hold W_p
+                // (8-row groups 256 bytes apart: W_p starts 512 p bytes in).
+                const uint32_t a0 = c.tmem + b2 * 64u, d = a0 + 32u;
+                umma_bf16_ts(d, a0, c.descB, umma_idesc(32), 0u);                              // x0 [W0|W1]
+                umma_bf16_ts(d + 16u, a0, c.descB + (1024u >> 4), umma_idesc(16), 1u);         // + x0 W2
+                umma_bf16_ts(d + 16u, a0 + 8u, c.descB, umma_idesc(16), 1u);                   // + x1 W0
+                umma_bf16_ts(d + 16u, a0 + 8u, c.descB + (512u >> 4), umma_idesc(16), 1u);     // + x1 W1
+                umma_bf16_ts(d + 16u, a0 + 16u, c.descB, umma_idesc(16), 1u);                  // + x2 W0
             } else {
                 umma_bf16(dcol, umma_sdesc(aoff), c.descB, umma_idesc(32), 0u);
                 umma_bf16(dcol + 16u, umma_sdesc(aoff + kTcPieceBytes), c.descB, umma_idesc(16), 1u);
@@ -265,18 +303,15 @@ __device__ __forceinline__ bool tc_mode(const TcCtx &c, float *S, uint32_t &phas
     const bool ok = mbar_wait(c.bar, phase);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float c0[16], c1[16], c2[16];
-    const uint32_t drow = c.tmem_row + (NP == 0 ? 32u : 0u);  // this thread's accumulator row
+    float c0[16], c1[16];
+    const uint32_t drow = c.tmem_row + (NP == 2 ? 0u : 32u);  // this thread's accumulator row
     tmem_ld16(drow, c0);
     tmem_ld16(drow + 16u, c1);
-    if (NP == 3) tmem_ld16(drow + 32u, c2);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     float y[16];
 #pragma unroll
     for (int n = 0; n < 16; n += 2) {
-        const float2 s = NP == 3 ? __fadd2_rn(__fadd2_rn(make_float2(c2[n], c2[n + 1]), make_float2(c1[n], c1[n + 1])),
-                                              make_float2(c0[n], c0[n + 1]))
-                                 : __fadd2_rn(make_float2(c1[n], c1[n + 1]), make_float2(c0[n], c0[n + 1]));
+        const float2 s = __fadd2_rn(make_float2(c1[n], c1[n + 1]), make_float2(c0[n], c0[n + 1]));
         y[n] = s.x, y[n + 1] = s.y;
     }
     if (D == 0) {
@@ -311,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) gtt_tc16_pass_kernel(const floa
     unsigned char *base = smem_raw + ((128u - (raw & 127u)) & 127u);
     float *ring = reinterpret_cast<float *>(base);
     unsigned char *A = base + kTcBufs * kTcTileBytes;
-    unsigned char *Bw = A + (NP == 0 ? 0 : 3 * kTcPieceBytes);
+    unsigned char *Bw = A + (NP == 2 ? 2 * kTcPieceBytes : 0);
     uint64_t *bar = reinterpret_cast<uint64_t *>(Bw + kTcWBytes);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(Bw + kTcWBytes + 8);
     const PassParams &p = tp.p;
