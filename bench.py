@@ -874,9 +874,34 @@ def extra_b2_f64(g, dev, hbm, reps=20):
             times["forward_plus_inverse"].append(s.elapsed_time(e) * 1e3)
     plan.check()
     y_h, z_h = yd.cpu().numpy(), zd.cpu().numpy()
+    # the same calls replayed from a CUDA graph (20 forward + inverse pairs per
+    # replay): device time without the host's per-call enqueue cost, which
+    # the single calls above include (a one-element torch op measures ~16 us)
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            plan.forward(xd, out=yd)
+            plan.inverse(yd, out=zd)
+    torch.cuda.synchronize()
+    graph, inner = torch.cuda.CUDAGraph(), 20
+    with torch.cuda.graph(graph):
+        for _ in range(inner):
+            plan.forward(xd, out=yd)
+            plan.inverse(yd, out=zd)
+    gt = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        graph.replay()
+        e.record()
+        torch.cuda.synchronize()
+        gt.append(s.elapsed_time(e) * 1e3 / inner)
+    plan.check()
     res = {"gpu_forward_us": statistics.median(times["forward"]),
            "gpu_forward_plus_inverse_us": statistics.median(times["forward_plus_inverse"]),
            "statistic": f"median of {reps} calls after 5 warm-ups", "passes": len(plan.describe()["passes"]),
+           "graph_forward_plus_inverse_us": statistics.median(gt),
+           "graph_statistic": f"median of {reps} replays of a graph of {inner} forward + inverse pairs",
            "tolerance": 1e-13}
 
     def dense_leg():

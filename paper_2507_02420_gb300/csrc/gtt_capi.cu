@@ -142,7 +142,16 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
                            std::vector<PassPlan> *out) {
     const int b = P->b, n = P->n, es = P->es;
     const int DM = dmax_bytes(es, b);
-    const long long tmax = std::max<long long>(max_tile_bytes / es, b);
+    long long tmax = std::max<long long>(max_tile_bytes / es, b);
+    // FP64 arithmetic runs at a small fraction of the FP32 rate, so a small
+    // FP64 / complex128 transform that one or two CTAs would hold is spread
+    // over many CTAs instead: tiles of at most b^3 elements, runs of 1.
+    // (b = 2, n = 12, FP64: 4 passes of 512 CTAs, 12.5 us per forward in a
+    // CUDA graph, against 32 us for one pass on one CTA.)
+    if ((P->dtype == GTT_F64 || P->dtype == GTT_C128) && P->total * es <= 2 * max_tile_bytes) {
+        tmax = std::min<long long>(tmax, (long long)b * b * b);
+        min_run_bytes = 0;
+    }
     std::vector<PassPlan> passes;
     int m0 = 0;
     while (m0 < n) {

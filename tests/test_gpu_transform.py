@@ -114,6 +114,26 @@ def test_b2_n12_f64_against_dense_oracle(g):
     assert rel_l2(xr, x) <= 1e-13
 
 
+def test_small_fp64_plan_spreads_over_many_ctas(g):
+    """A small FP64 transform is split into passes of at most 3 digits with
+    runs of 1 (FP64 runs at a small fraction of the FP32 rate, so one CTA per
+    pass would bind): b = 2, n = 12 takes 4 passes of 512 tiles, and a
+    complex128 b = 4, n = 6 plan (batch 1) 2 passes of 64 tiles; both against the dense
+    oracle."""
+    W, x = gi.workload_inputs("b2_n12_f64")
+    plan = g.Plan(W, 12, "f64", 1)
+    d = plan.describe()
+    assert len(d["passes"]) == 4 and all(p["grid"] >= 256 for p in d["passes"]), d
+    y = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel_l2(y[0], oracle.dense(W, x[0]).real) <= 1e-13
+    rng = np.random.default_rng(7300)
+    W4, x4 = make_inputs(4, 6, 1, "c128", rng)
+    p4 = g.Plan(W4, 6, "c128", 1)
+    assert len(p4.describe()["passes"]) == 2
+    y4 = p4.forward(torch.from_numpy(x4).cuda()).cpu().numpy()
+    assert rel_l2(y4, oracle.modes(W4, x4)) <= 1e-13
+
+
 def test_b4_n13_c64_full_size(g):
     """b=4, n=13 (N = 2^26), complex64, Haar W, in the default launch
     configuration: forward rel-L2 <= 1e-5, inverse(forward) vs x <= 2e-5,
