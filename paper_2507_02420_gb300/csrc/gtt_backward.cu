@@ -22,6 +22,7 @@
 #include <string>
 
 #include "gtt_bwd.cuh"
+#include "gtt_bwd8.cuh"
 #include "gtt_plan.h"
 
 using namespace gtt;
@@ -43,19 +44,32 @@ static size_t bwd_smem_bytes(int b, int g, long long tile, int es, bool cplx) {
     return (std::max(tiles, red) + 15) / 16 * 16;
 }
 
+static const void *bwd8_kernel(int g) {
+    return g == 4 ? (const void *)&gtt_backward_b8_kernel<4>
+                  : g == 3 ? (const void *)&gtt_backward_b8_kernel<3>
+                           : g == 2 ? (const void *)&gtt_backward_b8_kernel<2> : (const void *)&gtt_backward_b8_kernel<1>;
+}
+
 gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
     const int b = P->b, n = P->n, es = P->es;
     const bool cplx = P->dtype == GTT_C64 || P->dtype == GTT_C128;
     const int DM = dmax_bytes(es, b);
-    const void *bk = bwd_kernel((int)P->dtype, b);
-    if (!bk) return set_error(GTT_ERR_UNSUPPORTED, "no backward kernel for this dtype");
+    const void *bk_generic = bwd_kernel((int)P->dtype, b);
+    if (!bk_generic) return set_error(GTT_ERR_UNSUPPORTED, "no backward kernel for this dtype");
+    // FP32, b = 8: the fixed 4096-element tile kernel; the first pass takes
+    // digits 0-3, later passes at most 3 digits, so their runs are at least
+    // 8 elements (32 bytes)
+    const bool b8 = P->dtype == GTT_F32 && b == 8 && n >= 4;
     std::vector<BwdPass> out;
     int m0 = 0;
     while (m0 < n) {
         long long r = 1;
         const long long L = ipow_ll(b, m0);
         int g = 1;
-        if (m0 == 0) {
+        if (b8) {
+            g = m0 == 0 ? 4 : std::min(3, n - m0);
+            r = ipow_ll(8, 4 - g);
+        } else if (m0 == 0) {
             while (m0 + g < n && bwd_smem_bytes(b, g + 1, ipow_ll(b, g + 1), es, cplx) <= smem_budget) ++g;
         } else {
             // fewer passes first: as many modes as fit with runs of at least one
@@ -74,8 +88,9 @@ gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
         st = build_pass(P, m0, g, r, g >= DM ? DM : 1, &bp.fwd);  // forward recompute of a^(j+1)
         if (st != GTT_OK) return st;
         if (P->use_tma) tma_attach(P, &bp.fwd, P->tma_nbuf);  // stays on the CUDA-core kernel if ineligible
+        const void *bk = b8 ? bwd8_kernel(g) : bk_generic;
         bp.kern = bk;
-        bp.smem = bwd_smem_bytes(b, g, ipow_ll(b, g) * r, es, cplx);
+        bp.smem = b8 ? bwd8_smem_bytes(g) : bwd_smem_bytes(b, g, ipow_ll(b, g) * r, es, cplx);
         if (bp.smem > 227 * 1024) return set_error(GTT_ERR_UNSUPPORTED, "backward tile exceeds shared memory");
         cudaError_t e;
         e = allow_max_smem(bk, P->smem_optin);
@@ -87,8 +102,9 @@ gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
         if (per_sm < 1) return set_error(GTT_ERR_UNSUPPORTED, "backward kernel cannot be resident");
         bp.grid = (int)std::min<long long>((long long)per_sm * P->num_sms, bp.geo.params.tiles);
         static const char *tnames[] = {"f64", "f32", "c64", "c128", "u32"};
-        bp.name = std::string("gtt_backward_pass_kernel<") + tnames[(int)P->dtype] + "," +
-                  std::to_string(b) + "," + std::to_string(bwd_rows_host(b, cplx)) + ">";
+        bp.name = b8 ? "gtt_backward_b8_kernel<" + std::to_string(g) + ">"
+                     : std::string("gtt_backward_pass_kernel<") + tnames[(int)P->dtype] + "," +
+                           std::to_string(b) + "," + std::to_string(bwd_rows_host(b, cplx)) + ">";
         out.push_back(bp);
         m0 += g;
     }
