@@ -22,7 +22,7 @@
 #include <string>
 
 #include "gtt_bwd.cuh"
-#include "gtt_bwd8.cuh"
+#include "gtt_tile8.cuh"
 #include "gtt_plan.h"
 
 using namespace gtt;
@@ -87,7 +87,8 @@ gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget) {
         if (st != GTT_OK) return st;
         st = build_pass(P, m0, g, r, g >= DM ? DM : 1, &bp.fwd);  // forward recompute of a^(j+1)
         if (st != GTT_OK) return st;
-        if (P->use_tma) tma_attach(P, &bp.fwd, P->tma_nbuf);  // stays on the CUDA-core kernel if ineligible
+        if (!tile8_attach(P, &bp.fwd) && P->use_tma)
+            tma_attach(P, &bp.fwd, P->tma_nbuf);  // stays on the CUDA-core kernel if ineligible
         const void *bk = b8 ? bwd8_kernel(g) : bk_generic;
         bp.kern = bk;
         bp.smem = b8 ? bwd8_smem_bytes(g) : bwd_smem_bytes(b, g, ipow_ll(b, g) * r, es, cplx);

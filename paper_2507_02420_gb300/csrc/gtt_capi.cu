@@ -181,7 +181,7 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, D, &pp);
         if (st != GTT_OK) return st;
-        if (P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
+        if (!tile8_attach(P, &pp) && P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
         passes.push_back(pp);
         m0 += g;
     }
@@ -579,7 +579,7 @@ gtt_status_t make_explicit_schedule(gtt_plan_s *P, int count, const int *digits,
         PassPlan pp;
         gtt_status_t st = build_pass(P, m0, g, r, g >= DM ? DM : 1, &pp);
         if (st != GTT_OK) return st;
-        if (P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
+        if (!tile8_attach(P, &pp) && P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
         passes.push_back(pp);
         m0 += g;
     }

@@ -167,6 +167,9 @@ gtt_status_t make_tcx_schedule(gtt_plan_s *P, std::vector<PassPlan> *out);
 gtt_status_t tcx_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s);
 // Attach the TMA variant to a forward pass when its geometry allows (true if attached).
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
+// FP32 b = 8 passes on 4096-element tiles: the compile-time tile kernel
+// (false: the pass is not of that shape and stays as it is)
+bool tile8_attach(gtt_plan_s *P, PassPlan *pp);
 gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned char> &Wb, const void *in,
                      void *out, cudaStream_t stream, long long tile_begin, long long tile_end);
 // Zero elements [lo, hi) of every vector of y (batch x N, the plan's element

@@ -1,10 +1,13 @@
-// Backward pass for FP32 data with b = 8 on tiles of 4096 elements (four
-// base-8 digits), the top G of which the pass transforms; the low 4 - G digits
-// are a run of r = 8^(4-G) contiguous elements.  It computes what
-// gtt_backward_pass_kernel computes for these shapes (no counterpart in the
-// paper; PyTorch's convention: g_k = W^T applied to digit k of g_{k+1}, and
-// dW += sum over the fibres of digit k of g_{k+1}[i] a_k[j]), with the
-// tile geometry fixed at compile time:
+// FP32 passes with b = 8 on tiles of 4096 elements (four base-8 digits), the
+// top G of which a pass transforms; the low 4 - G digits are a run of
+// r = 8^(4-G) contiguous elements.  Two kernels share the tile machinery:
+//   - gtt_forward_b8_kernel<G>: a forward (or adjoint) pass, Algorithm 1's
+//     mode loop (Sec. 3) over the tile's top G digits;
+//   - gtt_backward_b8_kernel<G>: the reverse-mode pass (no counterpart in the
+//     paper; PyTorch's convention: g_k = W^T applied to digit k of g_{k+1},
+//     and dW += sum over the fibres of digit k of g_{k+1}[i] a_k[j]), which
+//     computes what gtt_backward_pass_kernel computes for these shapes.
+// The tile geometry is fixed at compile time:
 //   - element e = d0 + 8 d1 + 64 d2 + 512 d3 of the tile sits in shared
 //     memory at bwd8_pos(e) = e ^ 8 ((e >> 6) mod 4) ^ 4 ((e >> 5) mod 2);
 //     with one fibre per thread, every access of every digit is free of bank
@@ -12,9 +15,11 @@
 //     accesses whose 32 lanes hit 32 banks), and 16-byte chunks stay whole;
 //   - a fibre's 8 offsets are a per-fibre base combined with compile-time
 //     constants, so a mode costs no division or multiplication;
-//   - the activation and gradient tiles of the next tile are loaded with
-//     cp.async into a second buffer pair while this one is worked on.
-// Per tile: the activations entering digits 1 .. G-1 of the pass are
+//   - the next tile's inputs are loaded with cp.async into a second buffer
+//     (pair) while this one is worked on.
+// Forward, per tile: each of the G digits in turn, in place, 2 of the 512
+// fibres of a digit per thread; the tile is stored as 16-byte chunks.
+// Backward, per tile: the activations entering digits 1 .. G-1 of the pass are
 // recomputed into shared memory (W applied forward), then the digits are
 // walked in reverse, each thread owning 2 of the 512 fibres of a digit:
 // dW accumulates in 64 registers per thread across all the CTA's tiles and
@@ -256,6 +261,82 @@ gtt_backward_b8_kernel(const float *act_in, const float *grad_out, float *grad_i
         for (uint32_t th = 0; th < kBwd8Threads; ++th) sum += red[(size_t)th * 64 + tid];
         dw_part[(size_t)blockIdx.x * 64 + tid] = sum;
     }
+}
+
+// Shared memory of the b = 8 forward pass: the tile and the next one.
+constexpr size_t kFwd8Smem = 2 * kBwd8Tile * 4;
+
+// Tile digits LO .. LO + G - 1 in turn, in place.
+template <int G, int LO, int K>
+__device__ __forceinline__ void fwd8_digits(float *S, const WMat<float, 8> &W) {
+    if constexpr (K < G) {
+#pragma unroll 1
+        for (uint32_t i = 0; i < 2; ++i) bwd8_recompute<LO + K>(S, S, threadIdx.x + 256u * i, W);
+        __syncthreads();
+        fwd8_digits<G, LO, K + 1>(S, W);
+    }
+}
+
+// y = W applied to G digits of every tile (the adjoint passes W^H): the top G
+// tile digits over runs of 8^(4-G) elements (BOT = false), or, on the first
+// pass, the bottom G digits of 8^(4-G) consecutive blocks of 8^G elements
+// (BOT = true: a contiguous 4096-element tile).  In place is allowed: a tile
+// is read whole before it is written, and tiles are disjoint.
+template <int G, bool BOT>
+__global__ void __launch_bounds__(kBwd8Threads, 4) gtt_forward_b8_kernel(const float *in, float *out, PassParams p,
+                                                                         WMat<float, 8> W) {
+    constexpr uint32_t kLogR = BOT ? 0u : 3u * (4u - G);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    const uint32_t tid = threadIdx.x;
+    const long long LM = p.L * (long long)p.M;
+    auto tile_base = [&](long long t) {
+        if (BOT) return t * (long long)kBwd8Tile;  // contiguous tiles
+        const long long hi = t / p.lo_blocks;
+        const uint32_t lob = (uint32_t)(t - hi * p.lo_blocks);
+        return hi * LM + ((long long)lob << kLogR);
+    };
+    auto chunk_off = [&](long long gb, uint32_t c) {
+        const uint32_t e = 4u * c;
+        if (BOT) return gb + (long long)e;
+        return gb + (long long)(e >> kLogR) * p.L + (e & ((1u << kLogR) - 1u));
+    };
+    auto issue_load = [&](long long t, int s) {
+        if (t < p.tiles) {
+            const long long gb = tile_base(t);
+#pragma unroll
+            for (int i = 0; i < kBwd8Tile / 4 / kBwd8Threads; ++i) {
+                const uint32_t c = tid + (uint32_t)i * kBwd8Threads;
+                const long long go = GTT_CHECKED(chunk_off(gb, c), p.total - 3, p.err);
+                const uint32_t so = GTT_CHECKED(bwd8_pos(4u * c), kBwd8Tile - 3, p.err);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(sm + s * kBwd8Tile + so)),
+                             "l"(in + go)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const long long step = gridDim.x;
+    int s = 0;
+    issue_load(p.tile_begin + blockIdx.x, 0);
+    for (long long t = p.tile_begin + blockIdx.x; t < p.tiles; t += step) {
+        issue_load(t + step, s ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        float *S = sm + s * kBwd8Tile;
+        fwd8_digits<G, BOT ? 0 : 4 - G, 0>(S, W);
+        const long long gb = tile_base(t);
+#pragma unroll
+        for (int i = 0; i < kBwd8Tile / 4 / kBwd8Threads; ++i) {
+            const uint32_t c = tid + (uint32_t)i * kBwd8Threads;
+            const float4 v = *reinterpret_cast<const float4 *>(S + bwd8_pos(4u * c));
+            *reinterpret_cast<float4 *>(out + GTT_CHECKED(chunk_off(gb, c), p.total - 3, p.err)) = v;
+        }
+        __syncthreads();  // the buffer is read before the load two tiles ahead lands in it
+        s ^= 1;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 } // namespace gtt

@@ -134,6 +134,36 @@ def test_small_fp64_plan_spreads_over_many_ctas(g):
     assert rel_l2(y4, oracle.modes(W4, x4)) <= 1e-13
 
 
+@pytest.mark.parametrize("n,batch,passes", [(4, 3, None), (5, 3, None), (6, 2, None), (7, 1, None), (8, 1, None),
+                                             (7, 2, ([3, 4], [8, 1])), (7, 2, ([2, 2, 3], [64, 64, 8])),
+                                             (6, 3, ([1, 5], [512, 1]))])
+def test_b8_f32_tile_kernel_forward_and_adjoint(g, n, batch, passes):
+    """FP32, b = 8: passes on 4096-element tiles run the compile-time tile
+    kernel (top digits over runs of 8^(4-g), or the bottom digits of
+    consecutive blocks on the first pass).  Forward and adjoint of a
+    non-orthogonal W against the oracle, in place as well; other passes of
+    an explicit schedule keep their kernels."""
+    rng = np.random.default_rng(7200 + 10 * n + batch)
+    W = (rng.standard_normal((8, 8)) * 0.4).astype(np.float32)
+    x = gi.normal_x((batch, 8 ** n), rng, np.float32)
+    plan = g.Plan(W, n, "f32", batch)
+    if passes:
+        plan.set_passes(*passes)
+    d = plan.describe()
+    names = [p["kernel"] for p in d["passes"]]
+    assert any("gtt_forward_b8_kernel" in k for k in names), names
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    z = plan.inverse(xd)
+    w = xd.clone()
+    plan.forward(w, out=w)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(w, y)
+    assert rel_l2(y.cpu().numpy(), oracle.modes(up(W), up(x))) <= TOL["f32"], names
+    assert rel_l2(z.cpu().numpy(), oracle.adjoint(up(W), up(x))) <= TOL["f32"], names
+
+
 def test_b4_n13_c64_full_size(g):
     """b=4, n=13 (N = 2^26), complex64, Haar W, in the default launch
     configuration: forward rel-L2 <= 1e-5, inverse(forward) vs x <= 2e-5,
