@@ -26,10 +26,13 @@ bool tile8_attach(gtt_plan_s *P, PassPlan *pp) {
     if (g < 1 || g > 4 || pp->params.tile_elems != (uint32_t)kBwd8Tile) return false;
     long long r4 = 1;
     for (int i = g; i < 4; ++i) r4 *= 8;
+    // the kernel moves 16-byte chunks of 4 consecutive tile elements, so a
+    // later pass needs runs of at least 8 elements (g <= 3); the first pass
+    // has contiguous tiles
     bool bot;
     if (pp->m0 == 0)
         bot = g < 4;  // r = 8^(4-g) consecutive blocks (g = 4: the whole tile)
-    else if (pp->r == r4 && pp->params.r == (uint32_t)r4)
+    else if (g <= 3 && pp->r == r4 && pp->params.r == (uint32_t)r4)
         bot = false;
     else
         return false;

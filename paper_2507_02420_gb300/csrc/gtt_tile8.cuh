@@ -278,7 +278,9 @@ __device__ __forceinline__ void fwd8_digits(float *S, const WMat<float, 8> &W) {
 }
 
 // y = W applied to G digits of every tile (the adjoint passes W^H): the top G
-// tile digits over runs of 8^(4-G) elements (BOT = false), or, on the first
+// tile digits over runs of 8^(4-G) elements (BOT = false; G = 4 only on the
+// first pass, whose tiles are contiguous: the 16-byte chunk copies need runs
+// of at least 4 elements), or, on the first
 // pass, the bottom G digits of 8^(4-G) consecutive blocks of 8^G elements
 // (BOT = true: a contiguous 4096-element tile).  In place is allowed: a tile
 // is read whole before it is written, and tiles are disjoint.
