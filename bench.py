@@ -642,8 +642,17 @@ def extra_train(g, dev, hbm, reps=10):
     x3d = torch.from_numpy(x3).to(dev)
     y3d = torch.empty_like(x3d)
     dy3 = torch.from_numpy(gi.train_mask()).to(dev) * 2.0
+    ck3 = torch.empty_like(x3d)
+    try:  # the forward keeps the backward's checkpoint where the schedules allow it
+        p3.forward_saving(x3d, out=y3d, ckpt=ck3)
+        saving = True
+    except g.GTTError:
+        saving = False
 
     def train_step():
+        if saving:
+            p3.forward_saving(x3d, out=y3d, ckpt=ck3)
+            return p3.backward_saved(x3d, ck3, dy3)
         p3.forward(x3d, out=y3d)
         return p3.backward(x3d, dy3)
     t = _time_device(train_step, reps=reps)
@@ -664,7 +673,9 @@ def extra_train(g, dev, hbm, reps=10):
     res = {"ms": t * 1e3, "gelem_s": x3d.numel() / t / 1e9,
            "roofline": {"floor_ms": floor * 1e3, "frac": floor / t, "bound": "alu" if t_fma > t_mem else "hbm",
                         "basis": "max(5 x 4 B per element of HBM traffic, 4*n*b FMAs per element at the FP32 peak)"},
-           "includes": "gtt_forward + gtt_backward (dx and dW)", "schedule": "autotuned at plan time (untimed)",
+           "includes": ("gtt_forward_saving + gtt_backward_saved (dx and dW; the forward keeps the "
+                        "backward's checkpoint)" if saving else "gtt_forward + gtt_backward (dx and dW)"),
+           "schedule": "autotuned at plan time (untimed)",
            "forward_ms": tf * 1e3, "forward_l2chunked_ms": tc * 1e3,
            "tolerance": {"forward": 1e-5, "dx": 1e-5, "dW": 1e-4}}
 
@@ -675,7 +686,7 @@ def extra_train(g, dev, hbm, reps=10):
         return {"forward": rel_l2(y_h, oracle_modes(W3, x3)), "dx": rel_l2(dx_h, rdx), "dW": rel_l2(dW_h, rdW),
                 "basis": "whole batch (32 vectors), oracle gradient in FP64"}
     oracle_check(res, "rel_l2_vs_oracle", grad_errors)
-    del x3d, y3d, dy3, p3, dx3, dW3
+    del x3d, y3d, dy3, ck3, p3, dx3, dW3
     torch.cuda.empty_cache()
     return res
 

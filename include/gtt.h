@@ -254,6 +254,31 @@ gtt_status_t gtt_backward(gtt_plan_t plan, const void *x_saved, const void *dy, 
                           gtt_stream_t stream);
 
 /*
+ * gtt_forward_saving -- gtt_forward that also keeps, in ckpt, the activation
+ * entering the second pass of the plan's backward schedule (digits below the
+ * backward's split applied), which gtt_backward would otherwise recompute
+ * with an extra forward pass (not in the paper).  The forward runs its own
+ * schedule; the pass ending at the split writes ckpt, the next pass reads it.
+ *   x     device, batch*N elements (read).   y  device, batch*N (written).
+ *   ckpt  device, batch*N elements (written); must not alias x or y.
+ * Available when the backward schedule has two passes and the forward
+ * schedule has a pass boundary at its split digit (e.g. FP32 b = 8, n = 5..7,
+ * with the default schedule); otherwise GTT_ERR_UNSUPPORTED and nothing is
+ * launched.
+ */
+gtt_status_t gtt_forward_saving(gtt_plan_t plan, const void *x, void *y, void *ckpt, gtt_stream_t stream);
+
+/*
+ * gtt_backward_saved -- gtt_backward with the checkpoint that
+ * gtt_forward_saving wrote for the same x (and the same W): the backward
+ * passes only, no recompute pass.  Arguments as gtt_backward, plus ckpt
+ * (device, batch*N elements, read; distinct from x_saved and dy; dx may alias
+ * it).  GTT_ERR_UNSUPPORTED where gtt_forward_saving is.
+ */
+gtt_status_t gtt_backward_saved(gtt_plan_t plan, const void *x_saved, const void *ckpt, const void *dy, void *dx,
+                                void *dW, gtt_stream_t stream);
+
+/*
  * gtt_backward_noalloc -- the same results as gtt_backward, computed without
  * allocating any device memory (the paper has no counterpart to this call).
  * For callers that must not allocate on the device from inside the library:

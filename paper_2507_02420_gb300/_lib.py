@@ -39,6 +39,8 @@ SIGNATURES = {
     "gtt_forward": (_I, [_P, _P, _P, _P]),
     "gtt_inverse": (_I, [_P, _P, _P, _P]),
     "gtt_backward": (_I, [_P, _P, _P, _P, _P, _P]),
+    "gtt_forward_saving": (_I, [_P, _P, _P, _P, _P]),
+    "gtt_backward_saved": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "gtt_backward_noalloc": (_I, [_P, _P, _P, _P, _P, _P]),
     "gtt_filter": (_I, [_P, _P, _P, _LL, _I, _P]),
     "gtt_compress": (_I, [_P, _P, _P, _LL, _P, _P, _P]),

@@ -250,6 +250,35 @@ class Plan:
                                      _stream_ptr(stream)), "gtt_backward")
         return dx, dW
 
+    def forward_saving(self, x: torch.Tensor, out: torch.Tensor | None = None,
+                       ckpt: torch.Tensor | None = None, stream=None):
+        """gtt_forward_saving: y = G_N x, keeping in `ckpt` the activation that
+        backward_saved needs (so the backward recomputes nothing).  Returns
+        (y, ckpt); raises GTTError with status GTT_ERR_UNSUPPORTED (2) when
+        the plan's schedules allow no such checkpoint."""
+        self._check_dev(x, "x")
+        y = torch.empty_like(x) if out is None else out
+        ck = torch.empty_like(x) if ckpt is None else ckpt
+        self._check_dev(y, "out")
+        self._check_dev(ck, "ckpt")
+        check(self._lib.gtt_forward_saving(self._h, x.data_ptr(), y.data_ptr(), ck.data_ptr(), _stream_ptr(stream)),
+              "gtt_forward_saving")
+        return y, ck
+
+    def backward_saved(self, x: torch.Tensor, ckpt: torch.Tensor, dy: torch.Tensor, need_dx: bool = True,
+                       need_dW: bool = True, stream=None):
+        """gtt_backward_saved: backward() with the checkpoint from forward_saving."""
+        self._check_dev(x, "x")
+        self._check_dev(ckpt, "ckpt")
+        self._check_dev(dy, "dy")
+        dx = torch.empty_like(dy) if need_dx else None
+        dW = torch.empty((self.b, self.b), dtype=self.torch_dtype, device=dy.device) if need_dW and self.b else None
+        check(self._lib.gtt_backward_saved(self._h, x.data_ptr(), ckpt.data_ptr(), dy.data_ptr(),
+                                           dx.data_ptr() if dx is not None else None,
+                                           dW.data_ptr() if dW is not None else None,
+                                           _stream_ptr(stream)), "gtt_backward_saved")
+        return dx, dW
+
     # ------------------------------------------------------------ host calls
     def _host_arrays(self, x):
         xa = x.numpy() if isinstance(x, torch.Tensor) else np.asarray(x)

@@ -1,10 +1,12 @@
 """torch.autograd wrapper: y = G_N x with the library's hand-written adjoint.
 
 GTTFunction.apply(x, W, n) takes x of shape [batch, N] on a CUDA device and a
-b x b W (trainable).  The forward calls gtt_forward; the backward calls
-gtt_backward, which returns dL/dx = (W^H)^{(x)n} dL/dy and dL/dW as a per-mode
-reduction of fibre outer products (PyTorch's conjugate convention for complex
-types).  The kernels read W from their constant bank, so its values have to
+b x b W (trainable).  The forward calls gtt_forward_saving where the plan's
+schedules allow it (keeping the activation the backward would otherwise
+recompute, one vector-sized buffer held until the backward), else
+gtt_forward; the backward calls gtt_backward_saved or gtt_backward, which
+return dL/dx = (W^H)^{(x)n} dL/dy and dL/dW as a per-mode reduction of fibre
+outer products (PyTorch's conjugate convention for complex types).  The kernels read W from their constant bank, so its values have to
 be on the host when a kernel is launched: the wrapper copies W to the host only
 when it may differ from the last copy the plan took.  The plan's cache keeps a
 detached alias of the W it copied (so that storage cannot be freed and reused
@@ -21,6 +23,7 @@ import threading
 
 import torch
 
+from ._lib import GTTError
 from .api import Plan, dtype_code
 
 _cache: dict = {}
@@ -49,17 +52,30 @@ class GTTFunction(torch.autograd.Function):
             raise ValueError("x must have shape [batch, N]")
         x = x.contiguous()
         plan = _plan_for(W, n, x)
-        y = plan.forward(x)
-        ctx.save_for_backward(x, W)
+        ckpt = None
+        if getattr(plan, "_saving", True):
+            try:
+                y, ckpt = plan.forward_saving(x)
+            except GTTError as e:
+                if e.status != 2:  # GTT_ERR_UNSUPPORTED: this plan keeps no checkpoint
+                    raise
+                plan._saving = False
+        if ckpt is None:
+            y = plan.forward(x)
+            ckpt = x.new_empty(0)
+        ctx.save_for_backward(x, W, ckpt)
         ctx.n = n
         return y
 
     @staticmethod
     def backward(ctx, gy):
-        x, W = ctx.saved_tensors
+        x, W, ckpt = ctx.saved_tensors
         plan = _plan_for(W, ctx.n, x)
         need_dx, need_dW = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        dx, dW = plan.backward(x, gy.contiguous(), need_dx=need_dx, need_dW=need_dW)
+        if ckpt.numel():
+            dx, dW = plan.backward_saved(x, ckpt, gy.contiguous(), need_dx=need_dx, need_dW=need_dW)
+        else:
+            dx, dW = plan.backward(x, gy.contiguous(), need_dx=need_dx, need_dW=need_dW)
         if dW is not None:
             dW = dW.to(W.device, W.dtype)
         return dx, dW, None

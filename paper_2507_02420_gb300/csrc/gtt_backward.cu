@@ -130,8 +130,10 @@ static gtt_status_t ensure_buffer(void **buf, size_t *have, size_t need, const c
 
 } // namespace gtt
 
-extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy, void *dx, void *dW,
-                                     gtt_stream_t stream) {
+// ckpt: the activation entering the second backward pass, saved by
+// gtt_forward_saving (two-pass schedules), or NULL to recompute it.
+static gtt_status_t backward_impl(gtt_plan_t P, const void *x, const void *ckpt, const void *dy, void *dx, void *dW,
+                                  gtt_stream_t stream) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
     if (P->mixed) return set_error(GTT_ERR_UNSUPPORTED, "not available for mixed-radix plans");
     if (P->dtype == GTT_I32) return set_error(GTT_ERR_UNSUPPORTED, "backward needs a floating-point dtype");
@@ -151,6 +153,12 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
         if (st != GTT_OK) return st;
     }
     const int m = (int)P->bwd.size();
+    if (ckpt) {
+        if (saving_boundary(P) < 0)
+            return set_error(GTT_ERR_UNSUPPORTED, "this plan keeps no checkpoint (use gtt_backward)");
+        if (((uintptr_t)ckpt & 15u) || ckpt == x || ckpt == dy)
+            return set_error(GTT_ERR_INVALID_ARG, "ckpt must be 16-byte aligned and distinct from x and dy");
+    }
     const size_t data_bytes = (size_t)P->total * P->es;
     // gradient buffer
     void *GB = dx;
@@ -162,7 +170,7 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
     // checkpoint buffer
     void *CK = nullptr;
     const bool two_ck = m == 3 && GB != dy;  // a^(2) parked in the gradient buffer
-    if (m >= 2) {
+    if (m >= 2 && !ckpt) {
         if (m == 2 && dx && dx != dy) {
             CK = dx;
         } else {
@@ -189,7 +197,10 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
     // activations entering each backward pass, computed up front when they fit
     std::vector<const void *> act(m, x);
     bool upfront = false;
-    if (m == 2 || two_ck) {
+    if (ckpt) {
+        act[1] = ckpt;  // m == 2: nothing to recompute
+        upfront = true;
+    } else if (m == 2 || two_ck) {
         st = fwd_pass(0, x, CK);
         if (st != GTT_OK) return st;
         act[1] = CK;
@@ -232,4 +243,15 @@ extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy
         if (st != GTT_OK) return st;
     }
     return GTT_OK;
+}
+
+extern "C" gtt_status_t gtt_backward(gtt_plan_t P, const void *x, const void *dy, void *dx, void *dW,
+                                     gtt_stream_t stream) {
+    return backward_impl(P, x, nullptr, dy, dx, dW, stream);
+}
+
+extern "C" gtt_status_t gtt_backward_saved(gtt_plan_t P, const void *x, const void *ckpt, const void *dy, void *dx,
+                                           void *dW, gtt_stream_t stream) {
+    if (!ckpt) return set_error(GTT_ERR_INVALID_ARG, "NULL ckpt");
+    return backward_impl(P, x, ckpt, dy, dx, dW, stream);
 }

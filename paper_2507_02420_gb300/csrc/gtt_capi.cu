@@ -845,6 +845,48 @@ extern "C" gtt_status_t gtt_inverse(gtt_plan_t P, const void *y, void *x, gtt_st
     return transform(P, y, x, stream, true);
 }
 
+namespace gtt {
+// Index of the forward pass after which exactly the digits below the
+// backward's split digit are applied, or -1 (two-pass backward schedules only).
+int saving_boundary(gtt_plan_s *P) {
+    if (P->mixed || P->dtype == GTT_I32) return -1;
+    if (!P->bwd_ready && make_bwd_schedule(P, kBwdSmemBudget) != GTT_OK) return -1;
+    if (P->bwd.size() != 2) return -1;
+    const int split = P->bwd[1].geo.m0;
+    int done = 0;
+    for (size_t i = 0; i < P->passes.size(); ++i) {
+        if (P->passes[i].tcx.on) return -1;  // cluster passes cover digits by their own rule
+        done += P->passes[i].g;
+        if (done == split) return (int)i;
+        if (done > split) return -1;
+    }
+    return -1;
+}
+} // namespace gtt
+
+extern "C" gtt_status_t gtt_forward_saving(gtt_plan_t P, const void *x, void *y, void *ckpt, gtt_stream_t stream) {
+    if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");
+    if (!x || !y || !ckpt) return set_error(GTT_ERR_INVALID_ARG, "NULL data pointer");
+    if (!aligned16(x) || !aligned16(y) || !aligned16(ckpt))
+        return set_error(GTT_ERR_INVALID_ARG, "data pointers must be 16-byte aligned");
+    if (ckpt == x || ckpt == y) return set_error(GTT_ERR_INVALID_ARG, "ckpt must not alias x or y");
+    gtt_status_t st = check_device(P);
+    if (st != GTT_OK) return st;
+    const int k = saving_boundary(P);
+    if (k < 0)
+        return set_error(GTT_ERR_UNSUPPORTED,
+                         "no forward pass boundary at the backward's split digit (use gtt_forward + gtt_backward)");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t i = 0; i < P->passes.size(); ++i) {
+        PassPlan &pp = P->passes[i];
+        const void *in = i == 0 ? x : (i <= (size_t)k ? (const void *)ckpt : (i == (size_t)k + 1 ? ckpt : y));
+        void *out = i <= (size_t)k ? ckpt : y;
+        st = run_pass(P, pp, P->Wf, in, out, s, 0, pp.params.tiles);
+        if (st != GTT_OK) return st;
+    }
+    return GTT_OK;
+}
+
 static gtt_status_t transform_host(gtt_plan_t P, const void *xh, void *yh, gtt_stream_t stream,
                                    bool adjoint) {
     if (!P) return set_error(GTT_ERR_INVALID_ARG, "NULL plan");

@@ -149,6 +149,9 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 gtt_status_t launch_timed(gtt_plan_s *P, const void *kern, dim3 grid, dim3 block, void **args,
                           size_t smem, cudaStream_t stream, const std::string &name);
 gtt_status_t make_bwd_schedule(gtt_plan_s *P, size_t smem_budget);
+// Forward pass after which the digits below the backward's split are applied
+// (gtt_forward_saving's checkpoint), or -1.
+int saving_boundary(gtt_plan_s *P);
 // Autotuner (gtt_autotune.cu): apply a cached schedule to a plan (true if
 // one existed), or time candidates and keep the fastest.
 bool tune_apply_cached(gtt_plan_s *P);

@@ -123,6 +123,52 @@ def test_b8_f32_tile_kernel_matches_oracle_gradient(g, n, batch):
         assert rel(dyd.cpu().numpy(), rdx) <= TOL_DX["f32"] and rel(dWd.cpu().numpy(), rdW) <= TOL_DW["f32"]
 
 
+@pytest.mark.parametrize("n,batch", [(5, 3), (6, 2), (7, 1)])
+def test_forward_saving_and_backward_saved(g, n, batch):
+    """gtt_forward_saving keeps the backward's checkpoint; gtt_backward_saved
+    then runs the backward passes only.  y, dx and dW are bitwise equal to
+    gtt_forward + gtt_backward (the same kernels compute the checkpoint), and
+    dx and dW match the oracle gradient."""
+    rng = np.random.default_rng(5400 + n)
+    W, x, dy = inputs(8, n, batch, "f32", rng)
+    plan = g.Plan(W, n, "f32", batch)
+    xd, dyd = torch.from_numpy(x).cuda(), torch.from_numpy(dy).cuda()
+    y0 = plan.forward(xd)
+    dx0, dW0 = plan.backward(xd, dyd)
+    y1, ck = plan.forward_saving(xd)
+    dx1, dW1 = plan.backward_saved(xd, ck, dyd)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(y0, y1) and torch.equal(dx0, dx1) and torch.equal(dW0, dW1)
+    rdx, rdW = oracle.grad(up(W), up(x), up(dy))
+    assert rel(dx1.cpu().numpy(), rdx) <= TOL_DX["f32"] and rel(dW1.cpu().numpy(), rdW) <= TOL_DW["f32"]
+    # dx may alias the checkpoint
+    dWd = torch.empty((8, 8), device="cuda")
+    from paper_2507_02420_gb300 import _lib
+    st = _lib.load().gtt_backward_saved(plan._h, xd.data_ptr(), ck.data_ptr(), dyd.data_ptr(), ck.data_ptr(),
+                                        dWd.data_ptr(), None)
+    torch.cuda.synchronize()
+    assert st == 0 and torch.equal(ck, dx0) and torch.equal(dWd, dW0)
+
+
+@pytest.mark.parametrize("b,n,dt", [(8, 4, "f32"), (8, 8, "f32"), (2, 6, "f64")])
+def test_forward_saving_unsupported_shapes(g, b, n, dt):
+    """One-pass or three-pass backward schedules keep no checkpoint:
+    GTT_ERR_UNSUPPORTED, and the autograd wrapper falls back to the plain
+    calls (its gradient still matches the oracle)."""
+    rng = np.random.default_rng(5500 + b + n)
+    W, x, dy = inputs(b, n, 1, dt, rng)
+    plan = g.Plan(W, n, dt, 1)
+    with pytest.raises(g.GTTError) as ei:
+        plan.forward_saving(torch.from_numpy(x).cuda())
+    assert ei.value.status == 2
+    Wt = torch.from_numpy(W).cuda().requires_grad_(True)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    (g.gtt(xt, Wt, n) * torch.from_numpy(dy).cuda()).sum().backward()
+    rdx, rdW = oracle.grad(up(W), up(x), up(dy))
+    assert rel(xt.grad.cpu().numpy(), rdx) <= TOL_DX[dt] and rel(Wt.grad.cpu().numpy(), rdW) <= TOL_DW[dt]
+
+
 def test_three_pass_backward_uses_checkpoint_recompute(g):
     """A transform needing >= 3 backward passes (checkpoints recomputed)."""
     rng = np.random.default_rng(5100)
