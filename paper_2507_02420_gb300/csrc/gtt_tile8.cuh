@@ -146,6 +146,28 @@ __device__ __forceinline__ void bwd8_recompute(const float *A, float *An, uint32
     bwd8_store<T>(An, off, y);
 }
 
+// Forward digits T >= 1 with two fibres per thread: fibres 2p and 2p + 1
+// differ in tile digit 0 only, so their elements sit side by side (bwd8_pos
+// leaves bit 0 alone) and one 64-bit access serves both: half the
+// shared-memory instructions of two single-fibre calls (4 us faster on a
+// 4-digit pass of 67 M elements; the backward measured no gain from it).
+template <int T>
+__device__ __forceinline__ void bwd8_recompute2(const float *A, float *An, uint32_t pr, const WMat<float, 8> &W) {
+    static_assert(T >= 1, "pairs differ in tile digit 0");
+    uint32_t off[8];
+    bwd8_fibre<T>(2u * pr, off);
+    float ax[8], ay[8], yx[8], yy[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float2 v = *reinterpret_cast<const float2 *>(A + off[q]);
+        ax[q] = v.x, ay[q] = v.y;
+    }
+    bwd8_forward(ax, yx, W);
+    bwd8_forward(ay, yy, W);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) *reinterpret_cast<float2 *>(An + off[q]) = make_float2(yx[q], yy[q]);
+}
+
 // Activation entering the pass's digit K: the loaded tile for K = 0, else the
 // recomputed tile K - 1 after the four load buffers.
 template <int K> __device__ __forceinline__ float *bwd8_act(float *act0, float *sm) {
@@ -270,8 +292,11 @@ constexpr size_t kFwd8Smem = 2 * kBwd8Tile * 4;
 template <int G, int LO, int K>
 __device__ __forceinline__ void fwd8_digits(float *S, const WMat<float, 8> &W) {
     if constexpr (K < G) {
+        if constexpr (LO + K >= 1)
+            bwd8_recompute2<LO + K>(S, S, threadIdx.x, W);
+        else
 #pragma unroll 1
-        for (uint32_t i = 0; i < 2; ++i) bwd8_recompute<LO + K>(S, S, threadIdx.x + 256u * i, W);
+            for (uint32_t i = 0; i < 2; ++i) bwd8_recompute<LO + K>(S, S, threadIdx.x + 256u * i, W);
         __syncthreads();
         fwd8_digits<G, LO, K + 1>(S, W);
     }
