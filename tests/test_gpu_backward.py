@@ -151,6 +151,31 @@ def test_forward_saving_and_backward_saved(g, n, batch):
     assert st == 0 and torch.equal(ck, dx0) and torch.equal(dWd, dW0)
 
 
+@pytest.mark.parametrize("b,n,dt", [(16, 4, "f32"), (16, 5, "f32"), (4, 8, "c64"), (2, 14, "f32"), (3, 9, "c128"),
+                                    (5, 7, "f64")])
+def test_forward_saving_other_shapes(g, b, n, dt):
+    """Wherever gtt_forward_saving accepts a plan (the b = 16 tensor-core
+    schedule included), y is bitwise the plain forward's and the saved
+    backward matches the oracle gradient; elsewhere it is rejected with
+    GTT_ERR_UNSUPPORTED and launches nothing."""
+    rng = np.random.default_rng(5600 + b + n)
+    W, x, dy = inputs(b, n, 2, dt, rng)
+    plan = g.Plan(W, n, dt, 2)
+    xd, dyd = torch.from_numpy(x).cuda(), torch.from_numpy(dy).cuda()
+    y0 = plan.forward(xd)
+    try:
+        y1, ck = plan.forward_saving(xd)
+    except g.GTTError as e:
+        assert e.status == 2
+        return
+    dx, dW = plan.backward_saved(xd, ck, dyd)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(y0, y1)
+    rdx, rdW = oracle.grad(up(W), up(x), up(dy))
+    assert rel(dx.cpu().numpy(), rdx) <= TOL_DX[dt] and rel(dW.cpu().numpy(), rdW) <= TOL_DW[dt]
+
+
 @pytest.mark.parametrize("b,n,dt", [(8, 4, "f32"), (8, 8, "f32"), (2, 6, "f64")])
 def test_forward_saving_unsupported_shapes(g, b, n, dt):
     """One-pass or three-pass backward schedules keep no checkpoint:
