@@ -153,6 +153,25 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
         min_run_bytes = 0;
     }
     std::vector<PassPlan> passes;
+    // FP32, b = 8, default settings: the tile kernels' schedule, digits 0-3
+    // and then at most 3 digits on runs of 8^(4-g) (b8_n7: 245 us per forward
+    // against 302 us for the greedy [4, 2, 1])
+    if (P->dtype == GTT_F32 && b == 8 && n >= 4 && max_tile_bytes == kDefaultTileBytes &&
+        min_run_bytes == kDefaultRunBytes) {
+        for (int m = 0; m < n;) {
+            const int g = m == 0 ? 4 : std::min(3, n - m);
+            long long r = 1;
+            for (int i = g; m > 0 && i < 4; ++i) r *= 8;
+            PassPlan pp;
+            gtt_status_t st = build_pass(P, m, g, r, 1, &pp);
+            if (st != GTT_OK) return st;
+            if (!tile8_attach(P, &pp) && P->use_tma) tma_attach(P, &pp, P->tma_nbuf);
+            passes.push_back(pp);
+            m += g;
+        }
+        *out = passes;
+        return GTT_OK;
+    }
     int m0 = 0;
     while (m0 < n) {
         long long r = 1;
