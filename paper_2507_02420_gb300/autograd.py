@@ -53,7 +53,8 @@ class GTTFunction(torch.autograd.Function):
         x = x.contiguous()
         plan = _plan_for(W, n, x)
         ckpt = None
-        if getattr(plan, "_saving", True):
+        # keep the checkpoint only when a backward can follow
+        if (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]) and getattr(plan, "_saving", True):
             try:
                 y, ckpt = plan.forward_saving(x)
             except GTTError as e:
