@@ -114,12 +114,13 @@ gtt_status_t gtt_plan_create(gtt_plan_t *out, int b, int n, const void *W, gtt_d
  *   W        HOST pointer: W_0, W_1, ..., W_{n-1} back to back, each row-major
  *            b_k x b_k of `dtype`'s element type.
  * The plan runs CUDA-core passes over the digits, fastest first: adjacent
- * factors whose sizes multiply to at most 16 share one pass, which applies
+ * factors whose sizes multiply to at most 16 form one digit, transformed by
  * their Kronecker product (formed in double precision, or modulo 2^32 for
- * I32, and rounded once), every other factor has a pass of its own (gtt_forward,
- * gtt_inverse with the adjoints, the host-buffer calls, gtt_filter,
- * gtt_compress and gtt_decompress); gtt_plan_set_w takes the same
- * concatenated layout.  The
+ * I32, and rounded once); consecutive digits then share a pass, one stage
+ * per digit, as long as a tile of at most 48 KiB holds them, so most such
+ * transforms take one to three HBM round trips (gtt_forward, gtt_inverse
+ * with the adjoints, the host-buffer calls, gtt_filter, gtt_compress and
+ * gtt_decompress).  gtt_plan_set_w takes the same concatenated layout.  The
  * backward, explicit schedules and the autotuner return GTT_ERR_UNSUPPORTED
  * for such a plan.  Errors: GTT_ERR_INVALID_ARG (NULL pointers, n < 1, a b_k
  * outside [2, 16], sizes), GTT_ERR_ALLOC, GTT_ERR_CUDA.

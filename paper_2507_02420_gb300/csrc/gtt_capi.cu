@@ -214,8 +214,9 @@ gtt_status_t make_schedule(gtt_plan_s *P, long long max_tile_bytes, long long mi
 
 // Extend a row-major b x b matrix (element layout) to the kernels' parameter
 // layout WMat<T, B>: complex64 appends the pairs (re, re) and (-im, im) of
-// every entry; FP32 appends the row pairs (W[2i][j], W[2i+1][j]) (a single
-// unused pair for odd b); other types use the element layout as it is.
+// every entry; FP32 appends the row pairs (W[2i][j], W[2i+1][j]) (for odd b
+// the 4 bytes that align the pair array, then a single unused pair); other
+// types use the element layout as it is.  The result has the size of WMat<T, b>.
 static void append_packed_pairs(int dtype, int b, std::vector<unsigned char> *Wv) {
     if (dtype == GTT_C64) {
         std::vector<float> ex;
@@ -240,7 +241,7 @@ static void append_packed_pairs(int dtype, int b, std::vector<unsigned char> *Wv
                     ex.push_back(w[(2 * ip + 1) * b + j]);
                 }
         } else {
-            ex.assign(2, 0.f);
+            ex.assign(3, 0.f);
         }
         const unsigned char *p = reinterpret_cast<const unsigned char *>(ex.data());
         Wv->insert(Wv->end(), p, p + ex.size() * sizeof(float));
@@ -342,33 +343,49 @@ static std::vector<unsigned char> kron_factors(int dtype, int es, const std::vec
 }
 
 // Copy W into the plan: one matrix, or for a mixed plan the factors
-// W_0, ..., W_{n-1} back to back (each pass gets its own W and W^H: a single
-// factor, or the Kronecker product of the adjacent factors it covers).
-static void set_w_bytes(gtt_plan_s *P, const void *W) {
+// W_0, ..., W_{n-1} back to back; each stage of a mixed pass gets its own
+// factor and adjoint (a single factor, or the Kronecker product of the
+// adjacent factors it covers) in its slot of the pass's kernel parameters.
+static gtt_status_t set_w_bytes(gtt_plan_s *P, const void *W) {
     if (!P->mixed) {
         make_w_params((int)P->dtype, P->es, P->b, W, &P->Wf, &P->Wa);
-        return;
+        return GTT_OK;
     }
     const int n = P->n;
     std::vector<size_t> off(n + 1, 0);  // byte offset of factor k
     for (int k = 0; k < n; ++k) off[k + 1] = off[k] + (size_t)P->radices[k] * P->radices[k] * P->es;
+    size_t w_offset = 0, slot_bytes = 0;
+    int slots = 0;
+    const size_t args_bytes = mixed_args_bytes((int)P->dtype, &w_offset, &slot_bytes, &slots);
     for (PassPlan &pp : P->passes) {
-        const int hi = pp.factor, lo = pp.factor - pp.factors + 1;
-        if (pp.factors == 1) {
-            make_w_params((int)P->dtype, P->es, P->radices[hi], (const unsigned char *)W + off[hi], &pp.wf, &pp.wa);
-        } else {
-            const std::vector<unsigned char> K =
-                kron_factors((int)P->dtype, P->es, P->radices, off, (const unsigned char *)W, lo, hi);
-            int m = 1;
-            for (int k = lo; k <= hi; ++k) m *= P->radices[k];
-            make_w_params((int)P->dtype, P->es, m, K.data(), &pp.wf, &pp.wa);
+        MixPass &mx = pp.mix;
+        mx.args_f.assign(args_bytes, 0);
+        mx.args_a.assign(args_bytes, 0);
+        memcpy(mx.args_f.data(), &mx.params, sizeof(MixedParams));
+        memcpy(mx.args_a.data(), &mx.params, sizeof(MixedParams));
+        for (int k = 0; k < mx.params.nst; ++k) {
+            const int hi = mx.hi[k], lo = mx.hi[k] - mx.cnt[k] + 1;
+            std::vector<unsigned char> f, a;
+            if (mx.cnt[k] == 1) {
+                make_w_params((int)P->dtype, P->es, P->radices[hi], (const unsigned char *)W + off[hi], &f, &a);
+            } else {
+                const std::vector<unsigned char> K =
+                    kron_factors((int)P->dtype, P->es, P->radices, off, (const unsigned char *)W, lo, hi);
+                make_w_params((int)P->dtype, P->es, mx.params.rad[k], K.data(), &f, &a);
+            }
+            if (k >= slots || f.size() != wmat_size((int)P->dtype, mx.params.rad[k]) || f.size() > slot_bytes)
+                return set_error(GTT_ERR_INTERNAL, "factor layout size");
+            memcpy(mx.args_f.data() + w_offset + k * slot_bytes, f.data(), f.size());
+            memcpy(mx.args_a.data() + w_offset + k * slot_bytes, a.data(), a.size());
         }
     }
+    return GTT_OK;
 }
 
 extern "C" gtt_status_t gtt_plan_set_w(gtt_plan_t P, const void *W) {
     if (!P || !W) return set_error(GTT_ERR_INVALID_ARG, "NULL plan or W");
-    set_w_bytes(P, W);
+    gtt_status_t st = set_w_bytes(P, W);
+    if (st != GTT_OK) return st;
     if (P->precision == GTT_PREC_BF16X3 || P->precision == GTT_PREC_BF16X2 ||
         (P->precision == GTT_PREC_TF32X3 && P->b == 16))
         return tc_upload_w(P);
@@ -533,47 +550,83 @@ extern "C" gtt_status_t gtt_plan_create_mixed(gtt_plan_t *out, int n, const int 
         delete P;
         return cuda_error(e, "device query");
     }
-    // passes over the digits, the fastest index first: digit j of the natural
-    // index has radix b_{n-1-j} and stride L_j = prod_{i < j} b_{n-1-i}.
-    // Adjacent digits whose radices multiply to at most 16 form one digit of
-    // that radix (d_j + b_j d_{j+1} + ...), transformed by the Kronecker
-    // product of their factors (the slower digit's factor on the left): one
-    // round trip instead of several, for more FMAs per element.  A tile is
-    // kblk consecutive blocks of B rows (a row every L elements) of a run of r
-    // contiguous elements: r the product of the lowest radices, kblk the
-    // product of the next higher ones, as far as the default tile size allows
-    // (rows kblk * B at stride L address blocks hi .. hi + kblk - 1 in turn)
-    const long long tmax = kDefaultTileBytes / P->es;
-    auto rad = [&](int digit) { return (long long)radices[n - 1 - digit]; };
-    long long L = 1;
+    // digits, the fastest first: digit j of the natural index has radix
+    // b_{n-1-j} and stride prod_{i < j} b_{n-1-i}.  Adjacent digits whose
+    // radices multiply to at most 16 first become one digit of that radix
+    // (d_j + b_j d_{j+1} + ...), transformed by the Kronecker product of their
+    // factors (the slower digit's factor on the left).  Consecutive such digits
+    // then share a pass, one stage each, as many as a tile of at most the
+    // default tile size holds and the kernel has factor slots for (three or
+    // four): the first pass on contiguous tiles of several consecutive blocks,
+    // the later ones on M rows of runs of r contiguous elements (r divides the
+    // stride L: at least 64 bytes where L allows, then as long as the tile
+    // allows).
+    struct MDigit {
+        int rad, hi, cnt;
+    };
+    std::vector<MDigit> md;
     for (int j = 0; j < n;) {
-        int g = 1;
-        long long bj = rad(j);
-        while (j + g < n && bj * rad(j + g) <= 16) bj *= rad(j + g++);
-        long long r = 1, kblk = 1;
-        for (int i = 0; i < j && r * rad(i) * bj <= tmax; ++i) r *= rad(i);
-        for (int i = j + g; i < n && kblk * rad(i) * bj * r <= tmax; ++i) kblk *= rad(i);
-        PassPlan pp;
-        gtt_status_t st = build_pass_geom(P, (int)bj, L, 1, kblk, r, 1, &pp);
-        if (st != GTT_OK) {
-            delete P;
-            return st;
-        }
-        pp.m0 = j;
-        pp.factor = n - 1 - j;
-        pp.factors = g;
-        P->passes.push_back(pp);
-        L *= bj;
+        int g = 1, bj = radices[n - 1 - j];
+        while (j + g < n && bj * radices[n - 1 - (j + g)] <= 16) bj *= radices[n - 1 - (j + g++)];
+        md.push_back({bj, n - 1 - j, g});
         j += g;
     }
-    set_w_bytes(P, W);
-    e = cudaMalloc(&P->dev_err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(P->dev_err, 0, sizeof(int));
-    if (e != cudaSuccess) {
+    size_t w_offset = 0, slot_bytes = 0;
+    int max_stages = 0;  // factor slots in the mixed kernel's parameters
+    mixed_args_bytes((int)dtype, &w_offset, &slot_bytes, &max_stages);
+    const long long tmax = kDefaultTileBytes / P->es, rmin = std::max(1, 64 / P->es);
+    auto smallest_divisor_at_least = [](long long L, long long lo) {
+        for (long long d = lo; d < L; ++d)
+            if (L % d == 0) return d;
+        return L;
+    };
+    auto largest_divisor_at_most = [](long long L, long long hi) {
+        for (long long d = std::min(L, hi); d > 1; --d)
+            if (L % d == 0) return d;
+        return 1ll;
+    };
+    auto drop = [&](gtt_status_t st) {
         if (P->dev_err) cudaFree(P->dev_err);
         delete P;
-        return set_error(GTT_ERR_ALLOC, std::string("error flag: ") + cudaGetErrorString(e));
+        return st;
+    };
+    long long L = 1;
+    int digit = 0;
+    for (size_t i = 0; i < md.size();) {
+        long long r = L == 1 ? 1 : smallest_divisor_at_least(L, rmin);
+        if (r * md[i].rad > tmax) r = largest_divisor_at_most(L, tmax / md[i].rad);
+        long long M = md[i].rad;
+        size_t j = i + 1;
+        while (j < md.size() && j - i < (size_t)max_stages && M * md[j].rad * r <= tmax) M *= md[j++].rad;
+        if (L > 1) r = std::max(r, largest_divisor_at_most(L, tmax / M));  // longer runs where the tile has room
+        // the first pass: as many consecutive blocks per tile as it has room for
+        // (while the pass keeps at least two tiles per SM)
+        long long kblk =
+            L == 1 ? largest_divisor_at_most(P->total / M, std::min(tmax / M, P->total / M / (2ll * P->num_sms))) : 1;
+        std::vector<int> rad, hi, cnt;
+        int digits = 0;
+        for (size_t k = i; k < j; ++k) {
+            rad.push_back(md[k].rad);
+            hi.push_back(md[k].hi);
+            cnt.push_back(md[k].cnt);
+            digits += md[k].cnt;
+        }
+        PassPlan pp;
+        gtt_status_t st = build_mixed_pass(P, rad, hi, cnt, L, kblk, r, &pp);
+        if (st != GTT_OK) return drop(st);
+        pp.m0 = digit;
+        pp.factor = md[i].hi;
+        pp.factors = digits;
+        P->passes.push_back(pp);
+        L *= M;
+        digit += digits;
+        i = j;
     }
+    gtt_status_t st = set_w_bytes(P, W);
+    if (st != GTT_OK) return drop(st);
+    e = cudaMalloc(&P->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->dev_err, 0, sizeof(int));
+    if (e != cudaSuccess) return drop(set_error(GTT_ERR_ALLOC, std::string("error flag: ") + cudaGetErrorString(e)));
     *out = P;
     return GTT_OK;
 }
@@ -772,14 +825,22 @@ static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsi
     if (pp.tc.on) return tc_run(P, pp, &Wb == &P->Wa, in, outp, stream, tb, te);
     if (pp.tcx.on) return tcx_run(P, pp, &Wb == &P->Wa, in, outp, stream);
     if (pp.tma.on) return tma_run(P, pp, Wb, in, outp, stream, tb, te);
-    // a mixed plan's pass carries its own factor (W_k, or W_k^H for the adjoint)
-    const std::vector<unsigned char> &W = pp.factor < 0 ? Wb : (&Wb == &P->Wa ? pp.wa : pp.wf);
+    if (pp.mix.on) {  // a mixed plan's pass: its stages' factors (or their adjoints) in the parameters
+        std::vector<unsigned char> prm = &Wb == &P->Wa ? pp.mix.args_a : pp.mix.args_f;
+        MixedParams *m = reinterpret_cast<MixedParams *>(prm.data());
+        m->p.tile_begin = tb;
+        m->p.tiles = te;
+        m->p.err = P->dev_err;
+        const int grid = (int)std::min<long long>(pp.grid, te - tb);
+        void *args[3] = {(void *)&in, (void *)&outp, (void *)prm.data()};
+        return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
+    }
     PassParams prm = pp.params;
     prm.tile_begin = tb;
     prm.tiles = te;
     prm.err = P->dev_err;
     const int grid = (int)std::min<long long>(pp.grid, te - tb);
-    void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)W.data()};
+    void *args[4] = {(void *)&in, (void *)&outp, (void *)&prm, (void *)Wb.data()};
     return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
 }
 
@@ -968,6 +1029,13 @@ extern "C" gtt_status_t gtt_plan_describe(gtt_plan_t P, char *buf, size_t len) {
                  pp.tcx.on ? 1 : pp.tc.on ? pp.tc.ctas_per_sm : t ? pp.tma.ctas_per_sm : pp.ctas_per_sm, pp.params.vec_mode,
                  t ? "true" : "false", t ? pp.tma.params.nbuf : 0);
         s += tmp;
+        if (pp.mix.on) {  // the stages' radices, fastest digit first
+            s.pop_back();
+            s += ", \"radices\": [";
+            for (int k = 0; k < pp.mix.params.nst; ++k)
+                s += (k ? ", " : "") + std::to_string(pp.mix.params.rad[k]);
+            s += "], \"pad_shift\": " + std::to_string(pp.mix.params.pad_shift) + "}";
+        }
     }
     s += "]";
     if (P->bwd_ready) {  // the backward schedule, once a backward call has built it

@@ -6,6 +6,7 @@
 
 #include "../../include/gtt.h"
 #include "gtt_internal.h"
+#include "gtt_mixed.cuh"
 
 namespace gtt {
 
@@ -13,6 +14,17 @@ namespace gtt {
 // per SM) and runs of at least this many contiguous bytes in strided passes.
 constexpr long long kDefaultTileBytes = 48 * 1024;
 constexpr long long kDefaultRunBytes = 64;
+
+// Multi-factor pass of a mixed-radix plan (gtt_mixed.cuh): one stage per
+// digit, stage k applying the Kronecker product of the factors
+// W_{hi_k - cnt_k + 1} .. W_{hi_k} (a single factor when cnt_k = 1).
+struct MixPass {
+    bool on = false;
+    MixedParams params;
+    std::vector<int> hi, cnt;                  // factors of each stage
+    std::vector<unsigned char> args_f, args_a; // kernel parameters (MixedArgs<T>) with the factors or adjoints
+    MixPass() { memset(&params, 0, sizeof(params)); }
+};
 
 // One pass of a schedule: modes [m0, m0+g) with runs of r elements, register
 // windows of D digits, and its launch geometry.
@@ -70,10 +82,9 @@ struct PassPlan {
     TmaPass tma;
     TcPass tc;
     TcxPass tcx;
+    MixPass mix;                           // mixed plans: multi-factor pass (gtt_mixed.cuh)
     int factor = -1;                       // mixed plans: the factor W_k of the pass's fastest digit
-    int factors = 1;                       // mixed plans: adjacent factors W_{factor-factors+1} .. W_factor,
-                                           // applied as their Kronecker product (one digit of their sizes' product)
-    std::vector<unsigned char> wf, wa;     // mixed plans: that matrix and its adjoint, parameter layout
+    int factors = 1;                       // mixed plans: the factors W_{factor-factors+1} .. W_factor it applies
 };
 
 // One pass of the backward schedule: the tile geometry (one stage per digit),
@@ -168,6 +179,13 @@ bool tcx_eligible(const gtt_plan_s *P);
 gtt_status_t tcx_upload_w(gtt_plan_s *P);
 gtt_status_t make_tcx_schedule(gtt_plan_s *P, std::vector<PassPlan> *out);
 gtt_status_t tcx_run(gtt_plan_s *P, PassPlan &pp, bool adjoint, const void *in, void *out, cudaStream_t s);
+// Mixed-radix plans: a pass over consecutive digits of radices rad[0..] (fastest
+// first; stage k applies the factors hi[k] - cnt[k] + 1 .. hi[k]) at stride L,
+// runs of r, kblk blocks per tile.
+gtt_status_t build_mixed_pass(gtt_plan_s *P, const std::vector<int> &rad, const std::vector<int> &hi,
+                              const std::vector<int> &cnt, long long L, long long kblk, long long r, PassPlan *out);
+// Bytes of the kernels' parameter layout WMat<T, b> for a dtype code.
+size_t wmat_size(int dtype, int b);
 // Attach the TMA variant to a forward pass when its geometry allows (true if attached).
 bool tma_attach(gtt_plan_s *P, PassPlan *pp, int nbuf);
 // FP32 b = 8 passes on 4096-element tiles: the compile-time tile kernel

@@ -40,10 +40,29 @@ def rel(a, ref):
     return float(np.linalg.norm(up(a) - ref) / np.linalg.norm(ref))
 
 
+def merged_digits(radices):
+    """The plan's digits, fastest first: adjacent factors whose sizes multiply
+    to at most 16 form one digit (their Kronecker product)."""
+    out, j, digits = [], 0, radices[::-1]
+    while j < len(digits):
+        m = digits[j]
+        j += 1
+        while j < len(digits) and m * digits[j] <= 16:
+            m *= digits[j]
+            j += 1
+        out.append(m)
+    return out
+
+
 @pytest.mark.parametrize("radices,dt,batch", [([2, 3, 5, 7], "f64", 2), ([16, 2, 4], "c64", 3),
                                               ([3, 3, 8, 5, 2], "f32", 2), ([7, 11, 13], "c128", 1),
                                               ([16, 3, 9, 5, 7, 2, 2, 4, 11], "c64", 1),
-                                              ([2] * 12 + [3], "f32", 2)])
+                                              ([2] * 12 + [3], "f32", 2),
+                                              ([16, 3, 5, 7, 9, 11], "f32", 2),
+                                              ([13, 11, 7, 16, 9, 5], "c64", 2),
+                                              ([16] * 5, "c64", 4), ([3] * 9, "c128", 2),
+                                              ([11, 13, 7, 5, 3], "f64", 1),
+                                              ([5] * 8, "f32", 3), ([3] * 11, "c64", 4)])
 def test_mixed_forward_inverse_match_oracle(g, radices, dt, batch):
     rng = np.random.default_rng(10000 + len(radices))
     Ws, x = make(radices, batch, dt, rng)
@@ -56,16 +75,13 @@ def test_mixed_forward_inverse_match_oracle(g, radices, dt, batch):
     ref = oracle.modes_mixed([up(W) for W in Ws], up(x))
     assert rel(y.cpu().numpy(), ref) <= TOL[dt]
     assert rel(xr.cpu().numpy(), up(x)) <= 2 * TOL[dt]   # unitary factors: the adjoint inverts
-    # adjacent factors whose sizes multiply to at most 16 share a pass
-    want, j, digits = 0, 0, radices[::-1]
-    while j < len(digits):
-        m = digits[j]
-        j += 1
-        while j < len(digits) and m * digits[j] <= 16:
-            m *= digits[j]
-            j += 1
-        want += 1
-    assert len(plan.describe()["passes"]) == want
+    # consecutive digits share a pass, one stage each, while a tile of at most
+    # 48 KiB holds them: the stages of all passes are the merged digits in order
+    passes = plan.describe()["passes"]
+    assert [b for p in passes for b in p["radices"]] == merged_digits(radices)
+    assert all(p["kernel"].startswith("gtt_mixed_pass_kernel") and p["tile_bytes"] <= 48 * 1024 for p in passes)
+    if radices == [16, 3, 9, 5, 7, 2, 2, 4, 11]:
+        assert [p["radices"] for p in passes] == [[11, 16, 7], [5, 9, 3], [16]]
 
 
 def test_equal_factors_give_the_single_base_transform(g):
@@ -105,7 +121,8 @@ def test_mixed_integer_arithmetic_is_exact(g):
     np.testing.assert_array_equal(y.astype(np.int64), np.rint(ref).astype(np.int64))
 
 
-@pytest.mark.parametrize("radices", [[3, 2, 5, 4], [2, 2, 2, 2, 3], [16, 7, 2, 8], [4, 4, 3]])
+@pytest.mark.parametrize("radices", [[3, 2, 5, 4], [2, 2, 2, 2, 3], [16, 7, 2, 8], [4, 4, 3],
+                                     [16, 3, 5, 7, 9, 11]])
 def test_mixed_integer_wraps_modulo_2_32(g, radices):
     """int32 factors and data over the whole 32-bit range, so products and sums
     overflow: bit-exact against the oracle's mod-2^32 heterogeneous loop,
