@@ -164,7 +164,7 @@ __device__ __noinline__ void group_tile(const T *in, T *out, const PassParams &p
             T v[RB];
 #pragma unroll
             for (int q = 0; q < RB; ++q) v[q] = s[spos<RB>(e0 + q * strideA)];
-            apply_window<T, B, D>(v, mask, W);
+            apply_window<T, B, D, 0, false>(v, mask, W);  // W in shared memory: packed forms
 #pragma unroll
             for (int q = 0; q < RB; ++q) s[spos<RB>(e0 + q * strideA)] = v[q];
         }

@@ -19,7 +19,6 @@ namespace gtt {
 
 constexpr int kMixMaxStages = 4;
 constexpr int kMixThreads = 256;
-constexpr int kMixScalarFrom = 5;  // radices from which FP32 / complex64 stages use scalar FMAs
 
 // CTAs per SM the register budget aims at: three for 4- and 8-byte types
 // (measured best for complex64: 948 us against 963 us at two on the 9-factor
@@ -71,24 +70,7 @@ __device__ __forceinline__ void mixed_stage(T *__restrict__ s, const MixedArgs<T
             const uint32_t e = e0 + q * S;
             v[q] = s[GTT_CHECKED(e + (e >> ps), m.smem_elems, m.p.err)];
         }
-        if constexpr ((std::is_same<T, c64>::value || std::is_same<T, float>::value) && B >= kMixScalarFrom) {
-            // scalar FMAs with each factor entry as a constant-bank operand: the
-            // packed form's (re, re) / (-im, im) pairs of a large factor do not
-            // stay in registers, and moving a pair into registers costs more
-            // than the packing saves.  The same operations in the same order.
-            T in[B];
-#pragma unroll
-            for (int j = 0; j < B; ++j) in[j] = v[j];
-#pragma unroll
-            for (int i = 0; i < B; ++i) {
-                T acc = mul(W.w[i * B], in[0]);
-#pragma unroll
-                for (int j = 1; j < B; ++j) acc = fma_acc(W.w[i * B + j], in[j], acc);
-                v[i] = acc;
-            }
-        } else {
-            apply_digit<T, B, 1, 0>(v, W);
-        }
+        apply_digit<T, B, 1, 0, true, 16>(v, W);  // complex64: scalar FMAs from radix 5 on
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             const uint32_t e = e0 + q * S;

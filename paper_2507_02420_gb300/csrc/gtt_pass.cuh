@@ -57,14 +57,26 @@ template <int PADEVERY> __device__ __forceinline__ uint32_t spos(uint32_t e) {
     return e + e / PADEVERY;
 }
 
-// Apply W along register digit K of a B^D register block (stride B^K).
-template <typename T, int B, int D, int K>
+// Complex64 digits of radix 5 .. SMAX use scalar FMAs when W is a kernel
+// parameter (CW): the packed form's (re, re) / (-im, im) pairs of such a
+// matrix do not stay in registers, and moving each pair into registers before
+// its packed FMA costs more than the packing saves, while a scalar FMA takes
+// its W entry straight from the constant bank.  Measured per forward on
+// b^n x batch transforms: b = 5 904 -> 850 us, b = 8 1462 -> 1328 us, b = 7
+// even, b = 16 1934 -> 2000 us (so SMAX = 8 here; the mixed-radix kernel,
+// whose stages take W from parameter slots, gains at 16 too and passes 16).
+// FP32 keeps its packed row pairs: scalar FMAs measured slower there (b = 16
+// 1032 -> 1502 us, b = 12 281 -> 437 us).  With W in shared memory a pair is
+// one load either way, and the packed forms stay.  Both forms do the same
+// operations in the same order.
+template <typename T, int B, int D, int K, bool CW = true, int SMAX = 8>
 __device__ __forceinline__ void apply_digit(T (&v)[cpow(B, D)], const WMat<T, B> &W) {
     constexpr int S = cpow(B, K);
+    constexpr bool scalar = CW && std::is_same<T, c64>::value && B >= 5 && B <= SMAX;
 #pragma unroll
     for (int o = 0; o < cpow(B, D) / B; ++o) {
         const int base = (o / S) * S * B + (o % S);
-        if constexpr (std::is_same<T, c64>::value) {
+        if constexpr (std::is_same<T, c64>::value && !scalar) {
             // packed FP32x2: the same operations, in the same order, as mul/fma_acc
             float2 in[B], sw[B];
 #pragma unroll
@@ -88,7 +100,7 @@ __device__ __forceinline__ void apply_digit(T (&v)[cpow(B, D)], const WMat<T, B>
             }
 #pragma unroll
             for (int i = 0; i < B; ++i) v[base + i * S] = c64{acc[i].x, acc[i].y};
-        } else if constexpr (std::is_same<T, float>::value && B % 2 == 0) {
+        } else if constexpr (std::is_same<T, float>::value && B % 2 == 0 && !scalar) {
             float2 in[B];
 #pragma unroll
             for (int j = 0; j < B; ++j) in[j] = make_float2(v[base + j * S], v[base + j * S]);
@@ -119,12 +131,13 @@ __device__ __forceinline__ void apply_digit(T (&v)[cpow(B, D)], const WMat<T, B>
     }
 }
 
-// Apply W to every register digit K < D whose bit is set in `mask`.
-template <typename T, int B, int D, int K = 0>
+// Apply W to every register digit K < D whose bit is set in `mask` (CW: W is
+// a kernel parameter, false: W is in shared memory).
+template <typename T, int B, int D, int K = 0, bool CW = true>
 __device__ __forceinline__ void apply_window(T (&v)[cpow(B, D)], int mask, const WMat<T, B> &W) {
     if constexpr (K < D) {
-        if (mask & (1 << K)) apply_digit<T, B, D, K>(v, W);
-        apply_window<T, B, D, K + 1>(v, mask, W);
+        if (mask & (1 << K)) apply_digit<T, B, D, K, CW>(v, W);
+        apply_window<T, B, D, K + 1, CW>(v, mask, W);
     }
 }
 
