@@ -826,7 +826,9 @@ static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsi
     if (pp.tcx.on) return tcx_run(P, pp, &Wb == &P->Wa, in, outp, stream);
     if (pp.tma.on) return tma_run(P, pp, Wb, in, outp, stream, tb, te);
     if (pp.mix.on) {  // a mixed plan's pass: its stages' factors (or their adjoints) in the parameters
-        std::vector<unsigned char> prm = &Wb == &P->Wa ? pp.mix.args_a : pp.mix.args_f;
+        // (patched in place: the launch copies the parameters, and a plan is
+        // used from one host thread at a time)
+        std::vector<unsigned char> &prm = &Wb == &P->Wa ? pp.mix.args_a : pp.mix.args_f;
         MixedParams *m = reinterpret_cast<MixedParams *>(prm.data());
         m->p.tile_begin = tb;
         m->p.tiles = te;

@@ -167,6 +167,23 @@ def test_mixed_set_w_filter_and_codec(g):
     assert rel(rec, oracle.modes_mixed(adj, spec)) <= 1e-12
 
 
+def test_mixed_set_w_on_multi_factor_passes(g):
+    """New factors through gtt_plan_set_w reach every stage of every
+    multi-factor pass (forward and adjoint), without rebuilding the plan."""
+    rng = np.random.default_rng(10350)
+    radices = [16, 3, 9, 5, 7, 2, 2, 4, 11]
+    Ws, x = make(radices, 1, "c64", rng)
+    plan = g.Plan.mixed(Ws, "c64", 1)
+    assert len(plan.describe()["passes"]) == 3
+    Ws2, _ = make(radices, 1, "c64", rng)
+    plan.set_w(Ws2)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.forward(xd)
+    ref = oracle.modes_mixed([up(W) for W in Ws2], up(x))
+    assert rel(y.cpu().numpy(), ref) <= TOL["c64"]
+    assert rel(plan.inverse(y).cpu().numpy(), up(x)) <= 2 * TOL["c64"]
+
+
 def test_mixed_plan_rejections(g):
     rng = np.random.default_rng(10400)
     Ws, x = make([2, 3], 1, "f32", rng)
