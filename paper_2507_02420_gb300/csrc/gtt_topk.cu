@@ -15,16 +15,21 @@
 // number (T's lower bits are then zero), at the latest after the last digit.
 // The coefficients with key >= T are collected (exactly k), one CTA per
 // vector sorts them by key descending, and the values are gathered.
-// Before the radix passes, one pass histograms the top 12 bits of the keys and
-// a second pass collects every coefficient whose top bits reach the bucket
-// that holds the k-th largest key: a candidate list that contains all the k
-// largest keys, typically a few times k long.  The radix passes and the final
+// Before the radix passes, one pass over the spectrum histograms the top 12
+// bits of the keys and collects every coefficient whose top bits reach an
+// estimated bucket: the bucket that a sample of every 32nd coefficient puts
+// a little below the k-th largest key.  The exact histogram then shows
+// whether the estimate was low enough (the bucket of the k-th largest key is
+// not below it); if not, a second pass collects from that exact bucket.
+// Either way the list contains all the k largest keys, typically a few
+// times k long.  The radix passes and the final
 // collection then read the candidates instead of the spectrum.  A vector whose
 // candidates exceed the list's capacity (many equal magnitudes) keeps reading
 // its spectrum; the result is the same either way.
 // |c|^2 is formed with explicit round-to-nearest products and sum (no fused
 // multiply-add), so the decision can be reproduced in the same precision.
 #include <algorithm>
+#include <cmath>
 
 #include "gtt_plan.h"
 #include "gtt_types.cuh"
@@ -35,6 +40,8 @@ constexpr int kTopkMax = 4096;   // k per vector (one CTA sorts them in shared m
 constexpr int kTopkSortThreads = 1024;
 constexpr int kTopkBins = 4096;           // buckets of the pre-pass: the top 12 bits of the key
 constexpr uint32_t kTopkCandCap = 65536;  // candidate list capacity per vector
+constexpr int kTopkSample = 32;           // the threshold estimate samples one coefficient in 32:
+constexpr int kTopkSampleRun = 32;        // runs of 32 consecutive ones, every 1024
 
 template <typename T> struct KeyOf;
 template <> struct KeyOf<float> {
@@ -111,73 +118,104 @@ __device__ __forceinline__ void topk_for_each(const T *v, long long N, F fn) {
     }
 }
 
-// Pre-pass 1: histogram of the top 12 key bits of vector blockIdx.y.
+// Estimate pass: histogram of the top 12 key bits of a sample of vector
+// blockIdx.y, runs of kTopkSampleRun consecutive coefficients (whole cache
+// lines for a warp) every kTopkSample * kTopkSampleRun.
 template <typename T>
-__global__ void __launch_bounds__(256) gtt_topk_bins_kernel(const T *spec, long long N, uint32_t *bins) {
+__global__ void __launch_bounds__(256) gtt_topk_sample_kernel(const T *spec, long long N, uint32_t *sbins) {
     using K = typename KeyOf<T>::K;
     constexpr int SH = 8 * (int)sizeof(K) - 12;
+    constexpr long long kPeriod = (long long)kTopkSample * kTopkSampleRun;
     __shared__ uint32_t h[kTopkBins];
     for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const long long item = blockIdx.y;
+    const long long item = blockIdx.y, ns = (N + kPeriod - 1) / kPeriod * kTopkSampleRun;
     const T *v = spec + item * N;
-    topk_for_each<T>(v, N, [&](const T &x, long long) { atomicAdd(&h[(uint32_t)(KeyOf<T>::key(x) >> SH)], 1u); });
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < ns; j += (long long)gridDim.x * blockDim.x) {
+        const long long e = (j / kTopkSampleRun) * kPeriod + j % kTopkSampleRun;
+        if (e < N) atomicAdd(&h[(uint32_t)(KeyOf<T>::key(v[e]) >> SH)], 1u);
+    }
     __syncthreads();
-    uint32_t *g = bins + item * kTopkBins;
+    uint32_t *g = sbins + item * kTopkBins;
     for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x)
         if (h[i]) atomicAdd(&g[i], h[i]);
 }
 
 // The bucket of vector blockIdx.x that holds its k-th largest key (the
-// counts of the buckets from the top reach k there).
-__global__ void __launch_bounds__(256) gtt_topk_binscan_kernel(long long k, const uint32_t *bins, uint32_t *thr) {
+// counts of the buckets from the top reach k there).  With est (the exact
+// histogram after an estimated collection): redo = the exact bucket lies
+// below the estimate, and the vector's candidate count restarts at 0 for the
+// collection from the exact bucket.
+__global__ void __launch_bounds__(256) gtt_topk_binscan_kernel(long long k, const uint32_t *bins, uint32_t *thr,
+                                                               const uint32_t *est, uint32_t *cand_n,
+                                                               uint32_t *redo) {
     constexpr int PER = kTopkBins / 256;
     const long long item = blockIdx.x;
     const uint32_t *g = bins + item * kTopkBins;
+    const uint32_t tid = threadIdx.x;
+    const unsigned long long kk = (unsigned long long)k;
     __shared__ uint32_t h[kTopkBins];
-    __shared__ uint32_t part[256];
-    for (int i = threadIdx.x; i < kTopkBins; i += 256) h[i] = g[i];
+    __shared__ unsigned long long suf[256];
+    for (int i = tid; i < kTopkBins; i += 256) h[i] = g[i];
     __syncthreads();
     uint32_t sum = 0;
-    for (int i = 0; i < PER; ++i) sum += h[threadIdx.x * PER + i];
-    part[threadIdx.x] = sum;
+    for (int i = 0; i < PER; ++i) sum += h[tid * PER + i];
+    suf[tid] = sum;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long above = 0;
-        int chunk = 0;
-        for (int c = 255; c >= 0; --c) {
-            if (above + part[c] >= k) {
-                chunk = c;
-                break;
-            }
-            above += part[c];
-        }
-        int bin = chunk * PER;
-        for (int b = chunk * PER + PER - 1; b >= chunk * PER; --b) {
-            if (above + h[b] >= k) {
+    // suf[c] = count of the keys in chunks c .. 255 (a suffix sum in 8 steps)
+    for (int d = 1; d < 256; d <<= 1) {
+        const unsigned long long add = tid + d < 256u ? suf[tid + d] : 0ull;
+        __syncthreads();
+        suf[tid] += add;
+        __syncthreads();
+    }
+    // the chunk where the count from the top reaches k (one thread), or chunk 0
+    // with bucket 0 when the vector holds fewer keys than k
+    const unsigned long long above_chunk = tid < 255u ? suf[tid + 1] : 0ull;
+    const bool mine = (suf[tid] >= kk && above_chunk < kk) || (tid == 0 && suf[0] < kk);
+    if (mine) {
+        unsigned long long above = above_chunk;
+        int bin = (int)tid * PER;
+        for (int b = (int)tid * PER + PER - 1; b >= (int)tid * PER && suf[0] >= kk; --b) {
+            if (above + h[b] >= kk) {
                 bin = b;
                 break;
             }
             above += h[b];
         }
         thr[item] = (uint32_t)bin;
+        if (est) {
+            const bool again = (uint32_t)bin < est[item];
+            redo[item] = again ? 1u : 0u;
+            if (again) cand_n[item] = 0u;
+        }
     }
 }
 
 // Pre-pass 2: the candidates of vector blockIdx.y, every coefficient whose
 // top 12 key bits reach its threshold bucket (cand_n counts them all; at most
 // cap are stored).
+// With bins: also the exact histogram of the top 12 key bits (the estimated
+// collection).  With redo: only the vectors whose estimate was too high.
 template <typename T>
 __global__ void __launch_bounds__(256) gtt_topk_cand_kernel(const T *spec, long long N, const uint32_t *thr,
                                                             uint32_t cap, uint32_t *cand_n,
-                                                            typename KeyOf<T>::K *cand_key, uint32_t *cand_idx) {
+                                                            typename KeyOf<T>::K *cand_key, uint32_t *cand_idx,
+                                                            uint32_t *bins, const uint32_t *redo) {
     using K = typename KeyOf<T>::K;
     constexpr int SH = 8 * (int)sizeof(K) - 12;
+    __shared__ uint32_t h[kTopkBins];
     const long long item = blockIdx.y;
+    if (redo && !redo[item]) return;  // uniform over the CTA
+    if (bins) {
+        for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+    }
     const uint32_t tb = thr[item];
     const T *v = spec + item * N;
     topk_for_each<T>(v, N, [&](const T &x, long long e) {
         const K key = KeyOf<T>::key(x);
+        if (bins) atomicAdd(&h[(uint32_t)(key >> SH)], 1u);
         if ((uint32_t)(key >> SH) >= tb) {
             const uint32_t slot = atomicAdd(&cand_n[item], 1u);
             if (slot < cap) {
@@ -186,6 +224,12 @@ __global__ void __launch_bounds__(256) gtt_topk_cand_kernel(const T *spec, long 
             }
         }
     });
+    if (bins) {
+        __syncthreads();
+        uint32_t *g = bins + item * kTopkBins;
+        for (int i = threadIdx.x; i < kTopkBins; i += blockDim.x)
+            if (h[i]) atomicAdd(&g[i], h[i]);
+    }
 }
 
 // Histogram of digit `pass` over the matching keys of vector blockIdx.y.
@@ -360,25 +404,45 @@ __global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_sort_kernel(const T
 // A vector whose candidate list holds at most kTopkMax entries: sort the whole
 // list in one CTA, write its first k entries and mark the vector done, so the
 // radix passes, the collection and the sort above pass it by.
+// The list may be longer (an estimated collection): only the candidates in
+// or above the exact bucket of the k-th largest key (thr) take part, as long
+// as they fit.
 template <typename T>
 __global__ void __launch_bounds__(kTopkSortThreads) gtt_topk_fastsort_kernel(const T *spec, long long N, long long k,
                                                                              uint32_t cap, const uint32_t *cand_n,
                                                                              const typename KeyOf<T>::K *cand_key,
                                                                              const uint32_t *cand_idx,
                                                                              long long *out_idx, T *out_val,
-                                                                             TopkState *state) {
+                                                                             TopkState *state, const uint32_t *thr) {
     using K = typename KeyOf<T>::K;
+    constexpr int SH = 8 * (int)sizeof(K) - 12;
     __shared__ K sk[kTopkMax];
     __shared__ uint32_t si[kTopkMax];
+    __shared__ uint32_t s_n;
     const long long item = blockIdx.x;
     const uint32_t nc = cand_n[item];
-    if (nc > cap || nc > (uint32_t)kTopkMax) return;  // the radix passes select this vector
+    if (nc > cap) return;  // the radix passes select this vector (uniform over the CTA)
+    const uint32_t tb = thr[item];
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+        const K key = cand_key[item * cap + i];
+        if ((uint32_t)(key >> SH) >= tb) {
+            const uint32_t slot = atomicAdd(&s_n, 1u);
+            if (slot < (uint32_t)kTopkMax) {
+                sk[slot] = key;
+                si[slot] = cand_idx[item * cap + i];
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t m = s_n;
+    if (m > (uint32_t)kTopkMax) return;  // too many in the exact bucket: the radix passes (uniform)
     int P2 = 1;
-    while (P2 < (int)nc) P2 <<= 1;
-    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
-        const bool ok = i < (int)nc;
-        sk[i] = ok ? cand_key[item * cap + i] : (K)0;
-        si[i] = ok ? cand_idx[item * cap + i] : kTopkPad;
+    while (P2 < (int)m) P2 <<= 1;
+    for (int i = (int)m + threadIdx.x; i < P2; i += blockDim.x) {
+        sk[i] = (K)0;
+        si[i] = kTopkPad;
     }
     __syncthreads();
     topk_bitonic<K>(sk, si, P2);
@@ -404,7 +468,7 @@ __global__ void __launch_bounds__(256) gtt_topk_scatter_kernel(const long long *
 }
 
 template <typename T> struct TopkKernels {
-    static const void *bins() { return (const void *)&gtt_topk_bins_kernel<T>; }
+    static const void *sample() { return (const void *)&gtt_topk_sample_kernel<T>; }
     static const void *cand() { return (const void *)&gtt_topk_cand_kernel<T>; }
     static const void *hist() { return (const void *)&gtt_topk_hist_kernel<T>; }
     static const void *collect() { return (const void *)&gtt_topk_collect_kernel<T>; }
@@ -433,13 +497,13 @@ static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, lo
     const size_t sidx_bytes = al((size_t)B * k * sizeof(uint32_t));
     const size_t cn_bytes = al((size_t)B * sizeof(uint32_t));
     const size_t ar_bytes = al((size_t)B * sizeof(uint32_t));
-    const size_t bins_bytes = use_cand ? al((size_t)B * kTopkBins * sizeof(uint32_t)) : 0;
-    const size_t thr_bytes = use_cand ? al((size_t)B * sizeof(uint32_t)) : 0;
+    const size_t bins_bytes = use_cand ? al((size_t)B * kTopkBins * sizeof(uint32_t)) : 0;  // sample, then exact
+    const size_t thr_bytes = use_cand ? al((size_t)B * sizeof(uint32_t)) : 0;               // estimate, exact, redo
     const size_t ckey_bytes = use_cand ? al((size_t)B * cap * KB) : 0;
     const size_t cidx_bytes = use_cand ? al((size_t)B * cap * sizeof(uint32_t)) : 0;
     const size_t need =
-        st_bytes + h_bytes + key_bytes + sidx_bytes + cn_bytes + ar_bytes + bins_bytes + thr_bytes + ckey_bytes +
-        cidx_bytes;
+        st_bytes + h_bytes + key_bytes + sidx_bytes + cn_bytes + ar_bytes + 2 * bins_bytes + 3 * thr_bytes +
+        ckey_bytes + cidx_bytes;
     if (P->ws_topk_bytes < need) {
         if (P->ws_topk) cudaFree(P->ws_topk);
         P->ws_topk = nullptr;
@@ -464,9 +528,15 @@ static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, lo
     w += cn_bytes;
     uint32_t *arrive = reinterpret_cast<uint32_t *>(w);  // CTAs of a vector done with the current digit
     w += ar_bytes;
+    uint32_t *sbins = reinterpret_cast<uint32_t *>(w);
+    w += bins_bytes;
     uint32_t *bins = reinterpret_cast<uint32_t *>(w);
     w += bins_bytes;
+    uint32_t *thr_est = reinterpret_cast<uint32_t *>(w);
+    w += thr_bytes;
     uint32_t *thr = reinterpret_cast<uint32_t *>(w);
+    w += thr_bytes;
+    uint32_t *redo = reinterpret_cast<uint32_t *>(w);
     w += thr_bytes;
     void *cand_key = w;
     w += ckey_bytes;
@@ -479,7 +549,7 @@ static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, lo
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, h_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(arrive, 0, ar_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cand_n, use_cand ? 0 : 0xFF, (size_t)B * sizeof(uint32_t), s);
-    if (e == cudaSuccess && use_cand) e = cudaMemsetAsync(bins, 0, bins_bytes, s);
+    if (e == cudaSuccess && use_cand) e = cudaMemsetAsync(sbins, 0, 2 * bins_bytes, s);  // both histograms
     if (e != cudaSuccess) return cuda_error(e, "top-k workspace set-up");
     // pass geometry: blocks per vector so the whole batch fills the GPU
     const long long per_item = std::max<long long>(1, std::min<long long>((N + 2047) / 2048,
@@ -490,20 +560,37 @@ static gtt_status_t topk_select(gtt_plan_s *P, const void *spec, long long k, lo
     uint32_t cp = cap;
     gtt_status_t st;
     if (use_cand) {
-        void *bargs[3] = {(void *)&sp, (void *)&n, (void *)&bins};
-        st = launch_timed(P, TK::bins(), grid, dim3(256), bargs, 0, s, "gtt_topk_bins_kernel");
+        // the estimate: the bucket where a sample of every kTopkSample-th key
+        // reaches k / kTopkSample plus four standard deviations and 8, so that
+        // the k-th largest key is very rarely above it
+        const double kf = (double)k / kTopkSample;
+        long long m = (long long)std::ceil(kf + 4.0 * std::sqrt(kf) + 8.0);
+        uint32_t *nil = nullptr;
+        void *sargs[3] = {(void *)&sp, (void *)&n, (void *)&sbins};
+        st = launch_timed(P, TK::sample(), grid, dim3(256), sargs, 0, s, "gtt_topk_sample_kernel");
         if (st != GTT_OK) return st;
-        void *targs[3] = {(void *)&kk, (void *)&bins, (void *)&thr};
+        void *eargs[6] = {(void *)&m, (void *)&sbins, (void *)&thr_est, (void *)&nil, (void *)&nil, (void *)&nil};
+        st = launch_timed(P, (const void *)&gtt_topk_binscan_kernel, dim3((unsigned)B), dim3(256), eargs, 0, s,
+                          "gtt_topk_binscan_kernel");
+        if (st != GTT_OK) return st;
+        // one pass: the exact histogram and the candidates from the estimate
+        void *c1args[9] = {(void *)&sp,       (void *)&n,        (void *)&thr_est, (void *)&cp, (void *)&cand_n,
+                           (void *)&cand_key, (void *)&cand_idx, (void *)&bins,    (void *)&nil};
+        st = launch_timed(P, TK::cand(), grid, dim3(256), c1args, 0, s, "gtt_topk_cand_kernel");
+        if (st != GTT_OK) return st;
+        void *targs[6] = {(void *)&kk, (void *)&bins, (void *)&thr, (void *)&thr_est, (void *)&cand_n,
+                          (void *)&redo};
         st = launch_timed(P, (const void *)&gtt_topk_binscan_kernel, dim3((unsigned)B), dim3(256), targs, 0, s,
                           "gtt_topk_binscan_kernel");
         if (st != GTT_OK) return st;
-        void *cargs[7] = {(void *)&sp, (void *)&n, (void *)&thr, (void *)&cp, (void *)&cand_n, (void *)&cand_key,
-                          (void *)&cand_idx};
-        st = launch_timed(P, TK::cand(), grid, dim3(256), cargs, 0, s, "gtt_topk_cand_kernel");
+        // the vectors whose estimate was above their exact bucket collect again
+        void *c2args[9] = {(void *)&sp,       (void *)&n,        (void *)&thr, (void *)&cp,  (void *)&cand_n,
+                           (void *)&cand_key, (void *)&cand_idx, (void *)&nil, (void *)&redo};
+        st = launch_timed(P, TK::cand(), grid, dim3(256), c2args, 0, s, "gtt_topk_cand_kernel");
         if (st != GTT_OK) return st;
-        void *fargs[10] = {(void *)&sp,       (void *)&n,        (void *)&kk,      (void *)&cp,
+        void *fargs[11] = {(void *)&sp,       (void *)&n,        (void *)&kk,      (void *)&cp,
                            (void *)&cand_n,   (void *)&cand_key, (void *)&cand_idx, (void *)&out_idx,
-                           (void *)&out_val,  (void *)&state};
+                           (void *)&out_val,  (void *)&state,    (void *)&thr};
         st = launch_timed(P, TK::fastsort(), dim3((unsigned)B), dim3(kTopkSortThreads), fargs, 0, s,
                           "gtt_topk_fastsort_kernel");
         if (st != GTT_OK) return st;

@@ -137,6 +137,28 @@ def test_candidate_prepass_selection_is_exact(g, b, n, dt, batch, k):
     plan.check()
 
 
+def test_estimate_above_the_kth_key_collects_again(g):
+    """The threshold estimate samples every 32nd coefficient.  Vector 0 has
+    100 large coefficients, all at sampled indices, so the estimate lands on
+    their bucket although the 1024th largest key lies far below it: the exact
+    histogram catches this and the vector collects again from the exact
+    bucket.  Vector 1 has none and takes the estimate.  Both selections must
+    equal the host's.  (W = I, so the spectrum is x.)"""
+    rng = np.random.default_rng(9960)
+    n, k = 10, 1024
+    x = gi.complex_normal_x((2, 4 ** n), rng, np.complex64).astype(np.complex64)
+    x[0, 32 * np.arange(100)] = 100.0 + 50.0j
+    plan = g.Plan(np.eye(4, dtype=np.complex64), n, "c64", 2)
+    spec_d = torch.empty(2, 4 ** n, dtype=plan.torch_dtype, device="cuda")
+    idx, val = plan.compress(torch.from_numpy(x).cuda(), k, spectrum=spec_d)
+    spec = spec_d.cpu().numpy()
+    np.testing.assert_array_equal(spec, x)
+    np.testing.assert_array_equal(idx.cpu().numpy(), host_select(spec, k))
+    np.testing.assert_array_equal(val.cpu().numpy(), np.take_along_axis(spec, idx.cpu().numpy(), axis=1))
+    assert set(32 * np.arange(100)) <= set(idx.cpu().numpy()[0].tolist())
+    plan.check()
+
+
 def test_candidate_overflow_falls_back_to_the_spectrum(g):
     """2^20 equal magnitudes: every coefficient lands in one bucket, the
     candidate list overflows, and the selection reads the spectrum: the
