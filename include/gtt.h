@@ -333,8 +333,12 @@ gtt_status_t gtt_filter(gtt_plan_t plan, const void *x, void *y, long long cut, 
  *
  * gtt_decompress -- the reconstruction: y = G_N^dagger s for every vector,
  * where s holds values[v*k + j] at index indices[v*k + j] and zero elsewhere
- * (indices outside [0, N) are skipped; the result is not re-normalised).
- * y: device, batch*N elements.  Same errors.
+ * (indices outside [0, N) are skipped; of repeated indices one value is
+ * kept; the result is not re-normalised).  y: device, batch*N elements.
+ * Where the plan's first pass runs on contiguous tiles of the CUDA-core or
+ * TMA pass kernels, that pass runs only on the tiles holding kept indices
+ * (bitwise the same result); it uses the plan's selection workspace.  Same
+ * errors.
  */
 gtt_status_t gtt_compress(gtt_plan_t plan, const void *x, void *spectrum, long long k, long long *indices,
                           void *values, gtt_stream_t stream);

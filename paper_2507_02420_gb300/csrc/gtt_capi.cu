@@ -846,6 +846,15 @@ static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsi
     return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
 }
 
+gtt_status_t run_passes_from(gtt_plan_s *P, const std::vector<unsigned char> &Wb, void *y, cudaStream_t stream,
+                             size_t first) {
+    for (size_t i = first; i < P->passes.size(); ++i) {
+        gtt_status_t st = run_pass(P, P->passes[i], Wb, y, y, stream, 0, P->passes[i].params.tiles);
+        if (st != GTT_OK) return st;
+    }
+    return GTT_OK;
+}
+
 // Launch every pass of the schedule with the given W bytes.
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream) {

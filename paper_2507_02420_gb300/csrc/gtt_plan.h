@@ -198,4 +198,7 @@ gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned cha
 gtt_status_t zero_range(gtt_plan_s *P, void *y, long long lo, long long hi, cudaStream_t s);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
+// Passes first .. end of the schedule, in place on y, over all tiles (no chunking).
+gtt_status_t run_passes_from(gtt_plan_s *P, const std::vector<unsigned char> &Wb, void *y, cudaStream_t stream,
+                             size_t first);
 } // namespace gtt

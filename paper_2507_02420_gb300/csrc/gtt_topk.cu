@@ -32,6 +32,7 @@
 #include <cmath>
 
 #include "gtt_plan.h"
+#include "gtt_sparse.cuh"
 #include "gtt_types.cuh"
 
 namespace gtt {
@@ -622,6 +623,57 @@ static gtt_status_t topk_scatter(gtt_plan_s *P, const long long *idx, const void
     return launch_timed(P, TopkKernels<T>::scatter(), dim3(grid), dim3(256), args, 0, s, "gtt_topk_scatter_kernel");
 }
 
+// The reconstruction's first pass on the kept pairs only (gtt_sparse.cuh),
+// when the first pass is a CUDA-core or TMA pass (their stages are the sparse
+// kernel's) on contiguous tiles that divide a vector.  Returns false, with
+// nothing launched, when it does not apply.
+static bool sparse_first_applies(gtt_plan_s *P, long long k) {
+    if (P->mixed || P->passes.empty() || k > kSparseMaxK) return false;
+    const PassPlan &pp = P->passes[0];
+    if (pp.tc.on || pp.tcx.on || pp.mix.on || pp.m0 != 0) return false;
+    if (!pp.tma.on && pp.name.compare(0, 15, "gtt_pass_kernel") != 0) return false;  // e.g. the b = 8 tile kernel
+    const PassParams &p = pp.params;
+    if (p.L != (long long)p.r || P->N % p.tile_elems != 0 || P->N / p.tile_elems >= (long long)kSparseNoTile)
+        return false;
+    return sparse_first_kernel((int)P->dtype, P->b, pp.D) != nullptr;
+}
+
+static gtt_status_t sparse_first_pass(gtt_plan_s *P, const long long *idx, const void *val, long long k, void *y,
+                                      cudaStream_t s) {
+    const long long B = P->batch, N = P->N;
+    const size_t need = (size_t)B * k * sizeof(unsigned long long);
+    if (P->ws_topk_bytes < need) {  // the selection workspace, grown for the sorted pairs
+        if (P->ws_topk) cudaFree(P->ws_topk);
+        P->ws_topk = nullptr;
+        P->ws_topk_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->ws_topk, need);
+        if (e != cudaSuccess) {
+            P->ws_topk = nullptr;
+            return set_error(GTT_ERR_ALLOC, std::string("top-k workspace: ") + cudaGetErrorString(e));
+        }
+        P->ws_topk_bytes = need;
+    }
+    unsigned long long *sorted = static_cast<unsigned long long *>(P->ws_topk);
+    PassPlan &pp = P->passes[0];
+    PassParams prm = pp.params;
+    prm.err = P->dev_err;
+    uint32_t te = prm.tile_elems;
+    long long kk = k, n = N;
+    void *sargs[5] = {(void *)&idx, (void *)&kk, (void *)&n, (void *)&te, (void *)&sorted};
+    gtt_status_t st = launch_timed(P, sparse_sort_kernel(), dim3((unsigned)B),
+                                   dim3(kSparseSortThreads), sargs, 0, s, "gtt_sparse_sort_kernel");
+    if (st != GTT_OK) return st;
+    const void *kern = sparse_first_kernel((int)P->dtype, P->b, pp.D);
+    cudaError_t e = allow_max_smem(kern, P->smem_optin);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+    void *fargs[8] = {(void *)&idx, (void *)&val, (void *)&sorted, (void *)&kk,
+                      (void *)&n,   (void *)&y,   (void *)&prm,    (void *)P->Wa.data()};
+    st = launch_timed(P, kern, dim3((unsigned)k, (unsigned)B), dim3(pp.block), fargs, pp.smem, s,
+                      "gtt_sparse_first_kernel");
+    if (st != GTT_OK) return st;
+    return run_passes_from(P, P->Wa, y, s, 1);
+}
+
 } // namespace gtt
 
 using namespace gtt;
@@ -669,6 +721,7 @@ extern "C" gtt_status_t gtt_decompress(gtt_plan_t P, const long long *indices, c
     cudaStream_t s = (cudaStream_t)stream;
     st = zero_range(P, y, 0, P->N, s);
     if (st != GTT_OK) return st;
+    if (sparse_first_applies(P, k)) return sparse_first_pass(P, indices, values, k, y, s);
     switch (P->dtype) {
     case GTT_F32: st = topk_scatter<float>(P, indices, values, k, y, s); break;
     case GTT_F64: st = topk_scatter<double>(P, indices, values, k, y, s); break;

@@ -183,6 +183,39 @@ def test_keeping_everything_reconstructs_x(g):
     assert np.linalg.norm(up(rec) - up(x)) / np.linalg.norm(up(x)) <= 4e-6
 
 
+@pytest.mark.parametrize("b,n,dt,batch,k,layout", [(4, 10, "c64", 2, 1024, "random"), (2, 20, "f32", 1, 700, "random"),
+                                                    (8, 7, "f64", 3, 33, "one_tile"), (16, 5, "c128", 2, 100, "random"),
+                                                    (4, 13, "c64", 1, 4096, "clustered"), (2, 12, "f32", 2, 1, "random")])
+def test_decompress_first_pass_on_kept_pairs_is_bitwise_the_dense_inverse(g, b, n, dt, batch, k, layout):
+    """gtt_decompress runs its first pass only on the tiles that hold kept
+    pairs (after zero-filling y); the result must be bitwise the plain
+    inverse of the zero-filled spectrum with the pairs scattered into it.
+    Indices outside [0, N) are skipped."""
+    rng = np.random.default_rng(9970 + b + n + k)
+    W, _ = make(b, 1, 1, dt, rng)
+    N = b ** n
+    if layout == "one_tile":
+        idx = np.stack([rng.choice(64, size=k, replace=False) + 1000 for _ in range(batch)])
+    elif layout == "clustered":
+        idx = np.stack([rng.choice(N // 64, size=k, replace=False) * 7 % N for _ in range(batch)])
+    else:
+        idx = np.stack([rng.choice(N, size=k, replace=False) for _ in range(batch)])
+    idx = idx.astype(np.int64)
+    if k > 2:
+        idx[0, 0], idx[0, 1] = -1, N   # skipped
+    cplx = dt in ("c64", "c128")
+    val = (rng.standard_normal((batch, k)) + (1j * rng.standard_normal((batch, k)) if cplx else 0)).astype(NP[dt])
+    plan = g.Plan(W, n, dt, batch)
+    y = plan.decompress(torch.from_numpy(idx).cuda(), torch.from_numpy(val).cuda()).cpu().numpy()
+    spec = np.zeros((batch, N), NP[dt])
+    for v in range(batch):
+        ok = (idx[v] >= 0) & (idx[v] < N)
+        spec[v, idx[v][ok]] = val[v][ok]
+    want = plan.inverse(torch.from_numpy(spec).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(y, want)
+    plan.check()
+
+
 def test_codec_rejects_bad_arguments(g):
     rng = np.random.default_rng(9920)
     W, x = make(2, 6, 1, "f32", rng)
