@@ -7,8 +7,9 @@
 // output buffer is zero-filled, the kept pairs are sorted by tile, and one
 // CTA per touched tile builds the tile in shared memory from its pairs,
 // applies the pass's register stages (the same stages, in the same order, as
-// the pass kernels, so the result is bitwise that of the dense pass) and
-// writes it.  The remaining passes then run as usual.
+// the pass kernels, so every value equals the dense pass's; a zero tile gives
+// zeros either way, up to the sign of zero) and writes it.  The remaining
+// passes then run as usual.
 #pragma once
 #include "gtt_pass.cuh"
 
