@@ -846,6 +846,11 @@ static gtt_status_t run_pass(gtt_plan_s *P, PassPlan &pp, const std::vector<unsi
     return launch_timed(P, pp.kern, dim3(grid), dim3(pp.block), args, pp.smem, stream, pp.name);
 }
 
+gtt_status_t run_pass_range(gtt_plan_s *P, size_t i, const std::vector<unsigned char> &Wb, const void *in, void *out,
+                            cudaStream_t stream, long long tile_begin, long long tile_end) {
+    return run_pass(P, P->passes[i], Wb, in, out, stream, tile_begin, tile_end);
+}
+
 gtt_status_t run_passes_from(gtt_plan_s *P, const std::vector<unsigned char> &Wb, void *y, cudaStream_t stream,
                              size_t first) {
     for (size_t i = first; i < P->passes.size(); ++i) {

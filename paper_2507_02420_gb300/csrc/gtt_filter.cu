@@ -5,7 +5,10 @@
 //
 // The forward passes write the spectrum into y; one write-only kernel zeroes
 // the masked coefficient range of every vector (it reads nothing); the
-// adjoint passes then run in place on y.
+// adjoint passes then run in place on y.  The adjoint's first pass works on
+// contiguous tiles, and a tile inside the zeroed range stays zero, so that
+// pass runs only on the tiles that meet the kept range (the same values: a
+// zero tile gives zeros either way, up to the sign of zero).
 #include <algorithm>
 
 #include "gtt_plan.h"
@@ -67,5 +70,17 @@ extern "C" gtt_status_t gtt_filter(gtt_plan_t P, const void *x, void *y, long lo
     st = keep_low ? zero_range(P, y, cut, P->N, s) : zero_range(P, y, 0, cut, s);
     if (st != GTT_OK) return st;
     // back to the signal domain
-    return run_passes(P, P->Wa, y, y, s);
+    const PassPlan &p0 = P->passes[0];
+    const long long te = p0.params.tile_elems;
+    if (p0.tcx.on || p0.m0 != 0 || p0.params.L != (long long)p0.params.r || P->N % te != 0 || P->batch > 16)
+        return run_passes(P, P->Wa, y, y, s);
+    const long long lo = keep_low ? 0 : cut, hi = keep_low ? cut : P->N;
+    for (long long v = 0; v < P->batch; ++v) {
+        const long long t0 = (v * P->N + lo) / te, t1 = (v * P->N + hi + te - 1) / te;
+        if (t1 > t0) {
+            st = run_pass_range(P, 0, P->Wa, y, y, s, t0, t1);
+            if (st != GTT_OK) return st;
+        }
+    }
+    return run_passes_from(P, P->Wa, y, s, 1);
 }

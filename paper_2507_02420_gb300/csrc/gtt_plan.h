@@ -198,6 +198,9 @@ gtt_status_t tma_run(gtt_plan_s *P, PassPlan &pp, const std::vector<unsigned cha
 gtt_status_t zero_range(gtt_plan_s *P, void *y, long long lo, long long hi, cudaStream_t s);
 gtt_status_t run_passes(gtt_plan_s *P, const std::vector<unsigned char> &Wb, const void *x, void *y,
                         cudaStream_t stream);
+// Pass i of the schedule over its tiles [tile_begin, tile_end).
+gtt_status_t run_pass_range(gtt_plan_s *P, size_t i, const std::vector<unsigned char> &Wb, const void *in, void *out,
+                            cudaStream_t stream, long long tile_begin, long long tile_end);
 // Passes first .. end of the schedule, in place on y, over all tiles (no chunking).
 gtt_status_t run_passes_from(gtt_plan_s *P, const std::vector<unsigned char> &Wb, void *y, cudaStream_t stream,
                              size_t first);
