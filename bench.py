@@ -721,7 +721,8 @@ def extra_grouped(g, dev, hbm, reps=10, count=1000):
             errs[dt].append(rel_l2(yr, oracle_modes(Wr, xr)))
         return {dt: max(v) for dt, v in errs.items() if v} | {"requests_checked": len(got), "statistic": "max over requests"}
     out = {"ms": t * 1e3, "gelem_s": elems / t / 1e9, "requests": len(reqs), "elements": elems,
-            "kernel_launches_per_execute": 1, "work_items": d["work_items"],
+            "kernel_launches_per_execute": (1 if d["work_items"] else 0) + d.get("direct_launches", 0),
+            "direct_requests": d.get("direct_requests", 0), "work_items": d["work_items"],
             "hbm_gbs_one_round_trip": 2 * nbytes / t / 1e9,
             "roofline": {"floor_ms": floor * 1e3, "frac": floor / t,
                          "basis": "sum over requests of max(one HBM round trip, n*N*b FMAs (x4 complex) at the FP32 peak)"},

@@ -408,17 +408,21 @@ typedef struct {
  * (gtt_plan_autotune / GTT_AUTOTUNE_CACHE) or the fixed rule.  Work items are
  * (request, pass, tile); a pass of a request starts after the request's
  * previous pass (a bounded device-side wait; expiry raises GTT_ERR_TIMEOUT in
- * gtt_group_check).  The pointers in the requests are fixed for the group's
+ * gtt_group_check).  Requests of 2 MiB or more run instead as a chain of
+ * their shape's pass kernels (with their own W) on four side streams of the
+ * same graph, beside the persistent kernel.  The pointers in the requests are fixed for the group's
  * lifetime.  Errors: GTT_ERR_INVALID_ARG, GTT_ERR_UNSUPPORTED (b or dtype
  * outside the supported set), GTT_ERR_ALLOC, GTT_ERR_CUDA.
  */
 gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_request_t *reqs);
-/* Run every request of the group: one graph launch (a counter reset and one
- * kernel) on `stream`; the graph is captured on the first call. */
+/* Run every request of the group: one graph launch (a counter reset, the
+ * persistent kernel and the large requests' pass chains) on `stream`; the
+ * graph is captured on the first call. */
 gtt_status_t gtt_group_execute(gtt_group_t group, gtt_stream_t stream);
 /* Wait for the device; GTT_ERR_TIMEOUT if a bounded wait expired (then cleared). */
 gtt_status_t gtt_group_check(gtt_group_t group);
-/* One-line JSON: requests, elements, work items, segments, grid, shared memory. */
+/* One-line JSON: requests, elements, work items, segments, grid, shared
+ * memory, and the large requests run as pass chains (count, launches, streams). */
 gtt_status_t gtt_group_describe(gtt_group_t group, char *buf, size_t len);
 gtt_status_t gtt_group_destroy(gtt_group_t group);
 

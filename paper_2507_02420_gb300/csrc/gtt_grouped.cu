@@ -11,6 +11,26 @@
 
 using namespace gtt;
 
+namespace {
+// A request large enough to fill the GPU on its own runs on its shape's plan
+// (the TMA / tile pass kernels, with its own W) instead of the persistent
+// kernel: a chain of launches per request, the requests spread over
+// kGroupSideStreams capture streams, so that chains run side by side, and the
+// persistent kernel takes half its CTAs per SM to leave room for them.
+// Measured on the 1000-request workload (312 direct requests): 2 MiB and 4
+// streams 6.08-6.10 ms against 6.30 with the persistent kernel's full grid,
+// 6.66 with 8 streams, 8.84 with 1; 1 MiB and 512 KiB thresholds 6.7-6.8 ms
+// (at 8 streams); everything in the persistent kernel 7.98 ms.
+constexpr long long kGroupDirectBytes = 2ll << 20;
+constexpr int kGroupSideStreams = 4;
+struct DirectReq {
+    gtt_plan_s *P;                  // the shape's plan (owned by the group)
+    std::vector<unsigned char> W;   // this request's W (or W^H) in the kernels' parameter layout
+    const void *x;
+    void *y;
+};
+} // namespace
+
 struct gtt_group_s {
     int device = 0, count = 0;
     GroupReq *d_reqs = nullptr;
@@ -28,6 +48,11 @@ struct gtt_group_s {
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<DirectReq> direct;            // requests run as pass chains on their shapes' plans
+    std::vector<gtt_plan_s *> direct_plans;   // owned
+    cudaStream_t side[kGroupSideStreams] = {};
+    cudaEvent_t fork = nullptr, join[kGroupSideStreams] = {};
+    long long direct_launches = 0;
 };
 
 namespace {
@@ -43,6 +68,12 @@ gtt_status_t fail(gtt_group_s *G, gtt_status_t st) {
         if (G->d_counters) cudaFree(G->d_counters);
         if (G->d_err) cudaFree(G->d_err);
         if (G->capture_stream) cudaStreamDestroy(G->capture_stream);
+        for (gtt_plan_s *P : G->direct_plans) gtt_plan_destroy(P);
+        for (int i = 0; i < kGroupSideStreams; ++i) {
+            if (G->side[i]) cudaStreamDestroy(G->side[i]);
+            if (G->join[i]) cudaEventDestroy(G->join[i]);
+        }
+        if (G->fork) cudaEventDestroy(G->fork);
         delete G;
     }
     return st;
@@ -61,7 +92,8 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
 
     // one scratch plan per distinct (b, n, dtype) supplies the schedule
     std::map<std::tuple<int, int, int>, gtt_plan_s *> shapes;
-    std::vector<GroupReq> hreqs(count);
+    std::vector<GroupReq> hreqs;  // the persistent kernel's requests
+    std::vector<const gtt_plan_s *> direct_shape;
     std::vector<unsigned char> wblob;
     size_t max_w = 16, max_tile_smem = 0;
     gtt_status_t st = GTT_OK;
@@ -100,11 +132,19 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
         // grouped kernel stages its tiles itself
         gtt_plan_set_w(P, R.W);
         const std::vector<unsigned char> &Wb = R.inverse ? P->Wa : P->Wf;
+        if (P->N * P->es >= kGroupDirectBytes) {
+            G->direct.push_back(DirectReq{P, Wb, R.x, R.y});
+            if (std::find(direct_shape.begin(), direct_shape.end(), P) == direct_shape.end()) direct_shape.push_back(P);
+            G->direct_launches += (long long)P->passes.size();
+            G->total_elems += P->N;
+            continue;
+        }
         const size_t off = (wblob.size() + 15) / 16 * 16;
         wblob.resize(off + Wb.size());
         memcpy(wblob.data() + off, Wb.data(), Wb.size());
         max_w = std::max(max_w, (Wb.size() + 15) / 16 * 16);
-        GroupReq &gr = hreqs[q];
+        hreqs.emplace_back();
+        GroupReq &gr = hreqs.back();
         memset(&gr, 0, sizeof(gr));
         gr.x = R.x;
         gr.y = R.y;
@@ -125,18 +165,24 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
         G->total_elems += P->N;
     }
     G->distinct_shapes = (int)shapes.size();
-    for (auto &kv : shapes) gtt_plan_destroy(kv.second);
+    for (auto &kv : shapes) {
+        if (std::find(direct_shape.begin(), direct_shape.end(), kv.second) != direct_shape.end())
+            G->direct_plans.push_back(kv.second);  // kept: the direct requests run on it
+        else
+            gtt_plan_destroy(kv.second);
+    }
     if (st != GTT_OK) return fail(G, st);
     wblob.resize(wblob.size() + max_w, 0);  // every W read of max_w bytes stays inside the blob
 
     // work list: pass p of request q after pass p-1 of request q + lag
     std::vector<GroupSeg> segs;
-    std::vector<std::vector<int>> seg_of(count, std::vector<int>(kGroupMaxPass, -1));
+    const int pcount = (int)hreqs.size();
+    std::vector<std::vector<int>> seg_of(pcount, std::vector<int>(kGroupMaxPass, -1));
     long long items = 0;
-    for (int t = 0; t < count + (G->max_passes - 1) * kGroupLag; ++t)
+    for (int t = 0; t < pcount + (G->max_passes - 1) * kGroupLag; ++t)
         for (int p = 0; p < G->max_passes; ++p) {
             const int q = t - p * kGroupLag;
-            if (q < 0 || q >= count || p >= hreqs[q].npass) continue;
+            if (q < 0 || q >= pcount || p >= hreqs[q].npass) continue;
             GroupSeg sg;
             memset(&sg, 0, sizeof(sg));
             sg.req = q;
@@ -157,9 +203,10 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
 
     // device tables
     G->counter_bytes = sizeof(unsigned long long) + segs.size() * sizeof(unsigned int);
-    e = cudaMalloc(&G->d_reqs, hreqs.size() * sizeof(GroupReq));
-    if (e == cudaSuccess) e = cudaMalloc(&G->d_segs, segs.size() * sizeof(GroupSeg));
-    if (e == cudaSuccess) e = cudaMalloc(&G->d_item_seg, item_seg.size() * sizeof(unsigned int));
+    // (at least one entry each: a group may have no requests for the persistent kernel)
+    e = cudaMalloc(&G->d_reqs, std::max<size_t>(1, hreqs.size()) * sizeof(GroupReq));
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_segs, std::max<size_t>(1, segs.size()) * sizeof(GroupSeg));
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_item_seg, std::max<size_t>(1, item_seg.size()) * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&G->d_wblob, wblob.size());
     if (e == cudaSuccess) e = cudaMalloc(&G->d_counters, G->counter_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&G->d_err, sizeof(int));
@@ -197,9 +244,20 @@ extern "C" gtt_status_t gtt_group_create(gtt_group_t *out, int count, const gtt_
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGroupThreads, G->smem);
     if (e != cudaSuccess || per_sm < 1) return fail(G, set_error(GTT_ERR_UNSUPPORTED, "group kernel cannot be resident"));
-    G->grid = per_sm * sms;
+    G->grid = (G->direct.empty() || per_sm < 2 ? per_sm : per_sm / 2) * sms;
     e = cudaStreamCreateWithFlags(&G->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(G, cuda_error(e, "capture stream"));
+    if (!G->direct.empty()) {
+        e = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming);
+        for (int i = 0; i < kGroupSideStreams && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&G->side[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return fail(G, cuda_error(e, "side streams"));
+        // largest requests first, dealt round-robin over the side streams
+        std::stable_sort(G->direct.begin(), G->direct.end(),
+                         [](const DirectReq &a, const DirectReq &b) { return a.P->N > b.P->N; });
+    }
     *out = G;
     return GTT_OK;
 }
@@ -208,10 +266,35 @@ static gtt_status_t group_capture(gtt_group_s *G) {
     cudaStream_t s = G->capture_stream;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_error(e, "begin capture");
-    cudaMemsetAsync(G->d_counters, 0, G->counter_bytes, s);
-    void *args[1] = {(void *)&G->args};
-    cudaLaunchKernel((const void *)&gtt_grouped_kernel, dim3(G->grid), dim3(kGroupThreads), args, G->smem, s);
+    gtt_status_t st = GTT_OK;
+    const int sides = G->direct.empty() ? 0 : kGroupSideStreams;
+    // the side streams fork at the start, so the pass chains of the direct
+    // requests run beside the persistent kernel
+    if (sides) {
+        cudaEventRecord(G->fork, s);
+        for (int i = 0; i < sides; ++i) cudaStreamWaitEvent(G->side[i], G->fork, 0);
+    }
+    if (G->args.total_items > 0) {
+        cudaMemsetAsync(G->d_counters, 0, G->counter_bytes, s);
+        void *args[1] = {(void *)&G->args};
+        cudaLaunchKernel((const void *)&gtt_grouped_kernel, dim3(G->grid), dim3(kGroupThreads), args, G->smem, s);
+    }
+    for (size_t j = 0; j < G->direct.size() && st == GTT_OK; ++j) {
+        DirectReq &r = G->direct[j];
+        for (size_t i = 0; i < r.P->passes.size() && st == GTT_OK; ++i)
+            st = run_pass_range(r.P, i, r.W, i == 0 ? r.x : (const void *)r.y, r.y, G->side[j % sides], 0,
+                                r.P->passes[i].params.tiles);
+    }
+    for (int i = 0; i < sides; ++i) {
+        cudaEventRecord(G->join[i], G->side[i]);
+        cudaStreamWaitEvent(s, G->join[i], 0);
+    }
     e = cudaStreamEndCapture(s, &G->graph);
+    if (st != GTT_OK) {
+        if (G->graph) cudaGraphDestroy(G->graph);
+        G->graph = nullptr;
+        return st;
+    }
     if (e != cudaSuccess) return cuda_error(e, "end capture");
     e = cudaGraphInstantiate(&G->exec, G->graph, 0);
     if (e != cudaSuccess) return cuda_error(e, "graph instantiate");
@@ -237,6 +320,13 @@ extern "C" gtt_status_t gtt_group_check(gtt_group_t G) {
     int flag = 0;
     cudaError_t e = cudaMemcpy(&flag, G->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "reading the group error flag");
+    for (gtt_plan_s *P : G->direct_plans) {  // the direct requests' pass kernels raise their plan's flag
+        int f = 0;
+        e = cudaMemcpy(&f, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_error(e, "reading a plan error flag");
+        if (f) cudaMemset(P->dev_err, 0, sizeof(int));
+        flag |= f;
+    }
     if (flag) {
         cudaMemset(G->d_err, 0, sizeof(int));
         if (flag & 2) return set_error(GTT_ERR_INTERNAL, "an index check of the debug build failed in the grouped kernel");
@@ -249,9 +339,11 @@ extern "C" gtt_status_t gtt_group_describe(gtt_group_t G, char *buf, size_t len)
     if (!G || !buf || len == 0) return set_error(GTT_ERR_INVALID_ARG, "NULL group or buffer");
     snprintf(buf, len,
              "{\"requests\": %d, \"elements\": %lld, \"work_items\": %lld, \"segments\": %d, \"distinct_shapes\": %d, "
-             "\"max_passes\": %d, \"grid\": %d, \"block\": %d, \"smem\": %zu, \"kernel\": \"gtt_grouped_kernel\"}",
+             "\"max_passes\": %d, \"grid\": %d, \"block\": %d, \"smem\": %zu, \"kernel\": \"gtt_grouped_kernel\", "
+             "\"direct_requests\": %zu, \"direct_launches\": %lld, \"direct_streams\": %d}",
              G->count, G->total_elems, G->args.total_items, G->args.nsegs, G->distinct_shapes, G->max_passes,
-             G->grid, kGroupThreads, G->smem);
+             G->grid, kGroupThreads, G->smem, G->direct.size(), G->direct_launches,
+             G->direct.empty() ? 0 : kGroupSideStreams);
     return GTT_OK;
 }
 
