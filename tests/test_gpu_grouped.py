@@ -63,6 +63,30 @@ def test_small_mixed_group_matches_oracle(g):
         assert rel(rq["y"].cpu().numpy(), ref) <= 2e-6, (b, n, dt, inv)
 
 
+@pytest.mark.parametrize("with_small", [False, True])
+def test_large_requests_run_as_pass_chains(g, with_small):
+    """Requests of 2 MiB or more run as chains of their shape's pass kernels on
+    side streams of the group's graph (TMA, b = 8 tile and CUDA-core passes,
+    forward and inverse, several requests sharing one shape with different W);
+    a group of only such requests has no persistent-kernel work at all."""
+    specs = [(4, 10, "c64", False), (4, 10, "c64", True), (8, 7, "f32", False), (2, 20, "f32", True),
+             (16, 5, "c64", False), (3, 13, "f32", False)]
+    if with_small:
+        specs += [(4, 5, "c64", False), (5, 4, "f32", True), (2, 9, "f32", False)]
+    reqs, host = make_requests(specs, 8050 + int(with_small))
+    grp = g.Group(reqs)
+    d = grp.describe()
+    assert d["direct_requests"] == 6
+    assert (d["work_items"] > 0) == with_small
+    for _ in range(2):   # replays give the same result
+        grp.execute()
+        torch.cuda.synchronize()
+        grp.check()
+        for (b, n, dt, inv), rq, (W, x) in zip(specs, reqs, host):
+            ref = oracle.adjoint(up(W), up(x)) if inv else oracle.modes(up(W), up(x))
+            assert rel(rq["y"].cpu().numpy(), ref) <= 2e-6, (b, n, dt, inv)
+
+
 def test_group_replay_is_repeatable_and_in_place(g):
     specs = [(4, 9, "c64", False), (2, 14, "f32", False), (16, 3, "f32", True), (3, 8, "c64", False)]
     reqs, host = make_requests(specs, 8100)
