@@ -403,7 +403,7 @@ typedef struct {
 } gtt_request_t;
 
 /*
- * gtt_group_create -- plan `count` requests for one persistent launch.  Each
+ * gtt_group_create -- plan `count` requests for one graph launch.  Each
  * distinct (b, n, dtype) gets its mode-group schedule from the autotune cache
  * (gtt_plan_autotune / GTT_AUTOTUNE_CACHE) or the fixed rule.  Work items are
  * (request, pass, tile); a pass of a request starts after the request's
