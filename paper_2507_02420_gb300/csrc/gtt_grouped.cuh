@@ -1,5 +1,7 @@
 // Grouped persistent launch: many transforms of uneven b, n and dtype in one
-// kernel (each transform is the fast GTT of Sec. 3 with its own W).
+// kernel (each transform is the fast GTT of Sec. 3 with its own W).  The
+// group's graph runs the requests under 2 MiB here and the larger ones as
+// chains of their shapes' pass kernels beside it (gtt_grouped.cu).
 //
 // The work list is a sequence of segments; a segment is one pass of one
 // request, split into tiles (the tile geometry of gtt_pass_kernel).  CTAs take

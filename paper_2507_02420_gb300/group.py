@@ -1,7 +1,8 @@
 """Grouped transforms: the gtt_group_* calls of include/gtt.h (marshalling only).
 
-Group(requests) plans many transforms of uneven b, n and dtype for ONE
-persistent kernel launch captured in a CUDA graph; execute() replays it.
+Group(requests) plans many transforms of uneven b, n and dtype for one CUDA
+graph: a persistent kernel for the requests under 2 MiB and chains of pass
+kernels for the larger ones; execute() replays it.
 Each request is a dict with keys b, n, dtype ("f32" or "c64"), W (host
 array), x and y (CUDA tensors of b**n elements; y may be x), inverse (bool).
 """
