@@ -337,7 +337,8 @@ gtt_status_t gtt_filter(gtt_plan_t plan, const void *x, void *y, long long cut, 
  * kept; the result is not re-normalised).  y: device, batch*N elements.
  * Where the plan's first pass runs on contiguous tiles of the CUDA-core or
  * TMA pass kernels, that pass runs only on the tiles holding kept indices
- * (the same values); it uses the plan's selection workspace.  Same
+ * (the same values); it uses the plan's selection workspace, so compress
+ * and decompress calls of one plan on different streams must not overlap.  Same
  * errors.
  */
 gtt_status_t gtt_compress(gtt_plan_t plan, const void *x, void *spectrum, long long k, long long *indices,
